@@ -1,0 +1,231 @@
+"""Pixel-array oracle: plain CPU statement of the pixel array method.
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` are the only callers.
+It shares no code with the CUDA library (``paper_1609_00061_gb300``) and neither
+package imports the other.
+
+The arithmetic lives in ``pa_oracle.c`` (plain C, ``-O2 -ffp-contract=off``);
+this module only marshals numpy arrays into it and strings the pairwise
+contractions of a network together.
+
+Arrays are ``Arr`` objects: one byte per pixel (0/1), numpy shape = the
+resolutions of the array's variables, axes in the order of ``Arr.vars``.
+
+Functions (passages of Spivak et al., arXiv 1609.00061):
+  valid_tolerance   Sec. 3.2, Eq. (continuity): a valid tolerance for a polynomial
+  plot              Sec. 3.2, sample-in-center plot
+  gam               Sec. 3.3, Algorithm 1 (all arrays at once; tiny grids)
+  contract          Sec. 3.3 Eq. (GAM) on one two-array cluster (Sec. 3.5)
+  reduce            Eq. (GAM) with one array: OR over the dropped variables
+  solve             the whole method: plots, then one cluster after another
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pa_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libpa_oracle.so")
+_lib = None
+
+KIND_EQ, KIND_LE, KIND_LT = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile pa_oracle.c into oracle/_build/libpa_oracle.so (gcc, no FMA)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-std=c99",
+           "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i32p = ctypes.POINTER(ctypes.c_int)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.or_coeff_count.restype = ctypes.c_int64
+        lib.or_coeff_count.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.or_coeff_index.restype = ctypes.c_int64
+        lib.or_coeff_index.argtypes = [ctypes.c_int, ctypes.c_int, i32p]
+        lib.or_eval_poly.restype = ctypes.c_double
+        lib.or_eval_poly.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f64p]
+        lib.or_valid_tolerance.restype = ctypes.c_double
+        lib.or_valid_tolerance.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f64p, f64p, i32p]
+        lib.or_plot.restype = ctypes.c_int
+        lib.or_plot.argtypes = [ctypes.c_int, ctypes.c_int, f64p, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, f64p, f64p, i32p, u8p]
+        lib.or_gam.restype = ctypes.c_int
+        lib.or_gam.argtypes = [ctypes.c_int, i32p, ctypes.c_int, i32p, i32p,
+                               ctypes.POINTER(u8p), ctypes.c_int, i32p, u8p]
+        lib.or_contract_pair.restype = ctypes.c_int
+        lib.or_contract_pair.argtypes = [ctypes.c_int, i32p, u8p, ctypes.c_int, i32p, u8p,
+                                         ctypes.c_int, i32p, i32p, u8p]
+        lib.or_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def num_threads() -> int:
+    return int(_L().or_num_threads())
+
+
+# ----------------------------------------------------------------- polynomials
+def coeff_count(n: int, degree: int) -> int:
+    return int(_L().or_coeff_count(n, degree))
+
+
+def coeff_index(exps, degree: int) -> int:
+    """Index of exponent tuple ``exps`` in the graded lex coefficient order of
+    polynomials of total degree <= ``degree`` (-1 when the degree is too high)."""
+    e, ep = _i32(exps)
+    return int(_L().or_coeff_index(len(e), degree, ep))
+
+
+def eval_poly(degree: int, coeffs, x) -> float:
+    c, cp = _f64(coeffs)
+    xx, xp = _f64(x)
+    return float(_L().or_eval_poly(len(xx), degree, cp, xp))
+
+
+# ------------------------------------------------------------------- plotting
+@dataclass
+class Arr:
+    """A Boolean array over named variables (one uint8 per pixel)."""
+    data: np.ndarray
+    vars: tuple
+
+
+def valid_tolerance(degree: int, coeffs, lo, hi, res) -> float:
+    c, cp = _f64(coeffs)
+    l, lp = _f64(lo)
+    h, hp = _f64(hi)
+    r, rp = _i32(res)
+    return float(_L().or_valid_tolerance(len(r), degree, cp, lp, hp, rp))
+
+
+def plot(degree: int, coeffs, kind: int, eps: float, lo, hi, res, strict: bool = False) -> np.ndarray:
+    """Sample-in-center plot over the box prod [lo_p, hi_p) at resolutions res."""
+    c, cp = _f64(coeffs)
+    l, lp = _f64(lo)
+    h, hp = _f64(hi)
+    r, rp = _i32(res)
+    assert len(c) == coeff_count(len(r), degree)
+    out = np.zeros(tuple(int(v) for v in r), dtype=np.uint8)
+    rc = _L().or_plot(len(r), degree, cp, int(kind), float(eps), int(bool(strict)), lp, hp, rp,
+                      _u8(out))
+    assert rc == 0
+    return out
+
+
+def relation_eps(rel, axes) -> float:
+    """Tolerance of a relation: its own when given (>= 0), else a valid one."""
+    if rel.eps >= 0:
+        return float(rel.eps)
+    lo = [axes[v][0] for v in rel.vars]
+    hi = [axes[v][1] for v in rel.vars]
+    res = [axes[v][2] for v in rel.vars]
+    return valid_tolerance(rel.degree, rel.coeffs, lo, hi, res)
+
+
+def plot_relation(rel, axes, strict: bool = False) -> Arr:
+    """Plot a relation over its ports (a repeated variable gives a repeated port)."""
+    lo = [axes[v][0] for v in rel.vars]
+    hi = [axes[v][1] for v in rel.vars]
+    res = [axes[v][2] for v in rel.vars]
+    eps = relation_eps(rel, axes)
+    return Arr(plot(rel.degree, rel.coeffs, rel.kind, eps, lo, hi, res, strict), tuple(rel.vars))
+
+
+# ---------------------------------------------------------------- GAM
+def gam(link_res, arrays, port_links, out_links) -> np.ndarray:
+    """Algorithm 1 verbatim: all arrays at once over every link entry."""
+    lr, lrp = _i32(link_res)
+    nd, ndp = _i32([len(p) for p in port_links])
+    flat = [l for p in port_links for l in p]
+    pl, plp = _i32(flat if flat else [0])
+    ol, olp = _i32(list(out_links) if len(out_links) else [0])
+    arrs = [np.array(a, dtype=np.uint8, order="C") for a in arrays]
+    for a, p in zip(arrs, port_links):
+        assert a.shape == tuple(link_res[l] for l in p)
+    ptrs = (ctypes.POINTER(ctypes.c_uint8) * max(1, len(arrs)))(*[_u8(a) for a in arrs])
+    out = np.zeros(tuple(link_res[l] for l in out_links), dtype=np.uint8)
+    rc = _L().or_gam(len(lr), lrp, len(arrs), ndp, plp, ptrs, len(out_links), olp, _u8(out))
+    assert rc == 0
+    return out
+
+
+def contract(X: Arr, Y: Arr, keep, vres) -> Arr:
+    """One two-array cluster: OR over every variable of X or Y not in ``keep``."""
+    keep = tuple(int(v) for v in keep)
+    xv, xvp = _i32(X.vars if X.vars else [0])
+    yv, yvp = _i32(Y.vars if Y.vars else [0])
+    kv, kvp = _i32(keep if keep else [0])
+    vr, vrp = _i32(vres)
+    xd = np.array(X.data, dtype=np.uint8, order="C")
+    yd = np.array(Y.data, dtype=np.uint8, order="C")
+    out = np.zeros(tuple(int(vres[v]) for v in keep), dtype=np.uint8)
+    rc = _L().or_contract_pair(len(X.vars), xvp, _u8(xd), len(Y.vars), yvp, _u8(yd),
+                               len(keep), kvp, vrp, _u8(out))
+    assert rc == 0
+    return Arr(out, keep)
+
+
+def reduce(X: Arr, keep, vres) -> Arr:
+    """Eq. (GAM) with a single array: OR over the variables not in ``keep``."""
+    one = Arr(np.ones((), dtype=np.uint8), ())
+    return contract(X, one, keep, vres)
+
+
+def solve(axes, rels, exposed, strict: bool = False, order=None) -> Arr:
+    """The pixel array method end to end (Sec. 3.6).
+
+    Plots every relation, then clusters one array at a time into a running
+    product (left to right, or in ``order``), summing out each variable as soon
+    as no array still to come and no exposed variable uses it.  Any cluster tree
+    gives the same result (Sec. 3.3, associativity), so the order is the
+    simplest one."""
+    vres = [int(a[2]) for a in axes]
+    exposed = tuple(int(v) for v in exposed)
+    plots = [plot_relation(r, axes, strict) for r in rels]
+    seq = list(range(len(plots))) if order is None else list(order)
+    acc = Arr(np.ones((), dtype=np.uint8), ())
+    for pos, i in enumerate(seq):
+        later = set(exposed)
+        for j in seq[pos + 1:]:
+            later.update(plots[j].vars)
+        have = []
+        for v in tuple(acc.vars) + tuple(plots[i].vars):
+            if v in later and v not in have:
+                have.append(v)
+        acc = contract(acc, plots[i], tuple(have), vres)
+    return contract(acc, Arr(np.ones((), dtype=np.uint8), ()), exposed, vres)
