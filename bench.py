@@ -1,0 +1,313 @@
+"""Benchmark: Boolean-contraction throughput of the pixel array method on GB300.
+
+One step = one whole solve (pa_solve_network) of the chain network: 9 variables
+in [-3, 3) at 2048 pixels per axis, 8 binary cubics R_k(v_k, v_{k+1}) with N(0,1)
+coefficients, v1 and v9 exposed: 8 plots, the join order, 7 Boolean 2048^3
+contractions.  The metric is dense-equivalent Boolean pixel-ops per second
+(the naive cost r^Lambda of every join, Sec. 3.5) for the whole job.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own instance (seed + rank): weak scaling,
+no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Boolean contraction Gpixel-ops/s"
+UNIT = "Gpixel-ops/s"
+WORKLOAD = ("chain8_r2048: 9 vars in [-3,3) at 2048 px/axis, 8 binary cubics with N(0,1) "
+            "coefficients (seed 0x160900061+2), v1,v9 exposed; 8 plots + 7 Boolean 2048^3 joins")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------ clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    """The CPU oracle timed as it stands on the host cores (bounded sample)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1609_00061_gb300 import workloads as W
+    oracle.build()
+    sample = reference_sample(W)
+    for _ in range(args.warmup):
+        oracle.solve(sample.axes, sample.rels, sample.exposed)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(sample.axes, sample.rels, sample.exposed)
+        times.append(time.perf_counter() - t0)
+    ops = sample_ops(sample)
+    ms = 1e3 * sum(times) / len(times)
+    val = ops / (ms / 1e3) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample.meta["sample"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample.meta["sample"]},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def reference_sample(W):
+    """The first 256 of 2048 rows of v1 (same pixels, same coefficients) with the
+    first two relations: one 256x2048x2048 join, about a second of oracle work."""
+    full = W.chain(res=2048, nrel=8)
+    lo, hi, r = full.axes[0]
+    axes = [(lo, lo + (hi - lo) * 256 / 2048, 256)] + list(full.axes[1:3])
+    s = W.System("chain_sample", axes, full.rels[:2], (0, 2))
+    s.meta["sample"] = ("chain8_r2048 rows 0..255 of v1, relations R1,R2: 2 plots + one "
+                        "256x2048x2048 join per step")
+    return s
+
+
+def sample_ops(s):
+    vres = [a[2] for a in s.axes]
+    ops = 1.0
+    for v in set(s.rels[0].vars) | set(s.rels[1].vars):
+        ops *= vres[v]
+    return ops
+
+
+def cpu_baseline():
+    import oracle
+    from paper_1609_00061_gb300 import workloads as W
+    oracle.build()
+    s = reference_sample(W)
+    oracle.solve(s.axes, s.rels, s.exposed)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.solve(s.axes, s.rels, s.exposed)
+        n += 1
+        if time.perf_counter() - t0 > 10.0 or n >= 20:
+            break
+    dt = (time.perf_counter() - t0) / n
+    return {"value": sample_ops(s) / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": s.meta["sample"] + f", {n} repetitions"}
+
+
+# ------------------------------------------------------------------ our arm
+def roofline(kernels, stats_step, steps, peaks, clocks, sysm):
+    """Roofline of the kernel with the largest share of device time."""
+    if not kernels:
+        return None
+    name, (launches, total_ms) = max(kernels.items(), key=lambda kv: kv[1][1])
+    per_launch_s = total_ms / 1e3 / max(1, launches)
+    f_clk = 2070e6
+    if name == "plot_kernel":
+        # algorithmic work: the hoisted polynomial sum_j g_j y^j per pixel, D FMAs = 2D flops
+        D = max(r.degree for r in sysm.rels)
+        pixels_per_launch = stats_step["pixels_plotted"] / max(1, launches / steps)
+        flops = 2.0 * D * pixels_per_launch
+        peak = 2.0 * 152 * 128 * f_clk / 1e12   # FP32 FMA lanes x clock
+        ach = flops / per_launch_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                "share": total_ms / sum(v[1] for v in kernels.values())}
+    if name == "rowor_kernel":
+        # bytes the sparse row-OR must move at least: read A, B, write C (bit-packed)
+        joins = stats_step["n_joins"]
+        r = sysm.axes[0][2]
+        bytes_per_launch = 3.0 * r * r / 8
+        ach = bytes_per_launch / per_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6784.5)
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "share": total_ms / sum(v[1] for v in kernels.values()), "joins_per_step": joins}
+    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+            "unit": "GB/s", "frac": None, "traffic": None}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1609_00061_gb300 as pa
+    from paper_1609_00061_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    eng = pa.Engine(dev)
+    sysm = W.chain(res=2048, nrel=8, seed=W.SEED_BASE + 2 + rank)
+    out = pa.BitArray.empty(sysm.exposed, [sysm.axes[v][2] for v in sysm.exposed], dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
+
+    def step():
+        return pa.pa_solve_network(eng.ctx, sysm.axes, sysm.rels, sysm.exposed, out)
+
+    for _ in range(max(3, args.warmup)):
+        st = step()
+    torch.cuda.synchronize()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    pa.pa_profile_enable(eng.ctx, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k)             # 256 MiB write: L2 (129 MB) holds nothing of the last step
+        starts[k].record(stream)
+        st = step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    kernels = pa.pa_profile_read(eng.ctx)
+    pa.pa_profile_enable(eng.ctx, False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{dev}")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ops = st["pixel_ops_dense"]
+    value = world * ops / (ms_max / 1e3) / 1e9
+
+    # end to end through the public call: host coefficients in, output words out
+    host_out = torch.empty(out.words.numel(), dtype=torch.int64, pin_memory=True)
+    h2d = sum(r.coeffs.nbytes for r in sysm.rels) + 20 * len(sysm.axes)
+    for _ in range(2):
+        step()
+        host_out.copy_(out.words, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step()
+        host_out.copy_(out.words, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{dev}")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * ops / float(e2e_t.item()) / 1e9
+
+    if rank != 0:
+        eng.close()
+        return
+    peaks = load_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write)",
+                   "pixel_ops_per_step": ops, "parallelism": f"independent systems x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(out.words.numel() * 8)},
+        "gpu_launches": int(st["n_launches"]) * args.steps,
+        "clocks": clk,
+        "roofline": roofline(kernels, st, args.steps, peaks, clk, sysm),
+        "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items()},
+        "stats": st,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * pa.h -- C interface of the GB300 pixel array engine.
+ *
+ * The pixel array method (Spivak, Dobson, Kumari, Wu, arXiv 1609.00061) solves a
+ * system of relations over a box by (1) plotting each relation as a Boolean
+ * pixel array (Sec. 3.2, sample-in-center plot) and (2) combining the plots by
+ * generalized array multiplication over the Boolean semiring (Sec. 3.3,
+ * Algorithm 1 and Eq. GAM), one cluster at a time (Sec. 3.5), until only the
+ * exposed variables remain (Sec. 3.6).
+ *
+ * Every entry point takes plain pointers and sizes.  Device work is enqueued on
+ * the CUDA stream passed as `stream` (a cudaStream_t cast to void*; NULL is the
+ * legacy default stream) and is asynchronous to the host unless stated.
+ *
+ * ---------------------------------------------------------------- conventions
+ * Variables are numbered 0..nvars-1.  Variable v ranges over [lo, hi) at
+ * resolution res >= 2 (Sec. 3.1, Definition of a pack): pixel i (0-based) of v
+ * covers [lo + i*delta, lo + (i+1)*delta) with delta = (hi - lo) / res, and its
+ * centre is computed as lo + ((double)i + 0.5) * delta (two IEEE roundings).
+ *
+ * Relations are polynomials f(x_1..x_n) compared with 0 (pa_kind).  The
+ * coefficients of all monomials of total degree <= degree are given in graded
+ * lexicographic order: total degree 0, 1, ..., degree; within one degree the
+ * exponent tuples (e_1, ..., e_n) in descending lexicographic order.  Two
+ * variables, degree 3: 1, x, y, x^2, xy, y^2, x^3, x^2y, xy^2, y^3.  f is evaluated
+ * in IEEE double precision without fused multiply-add, in the nested form
+ *   f = sum_{e_n} ( ... ( sum_{e_1} c_e * x_1^{e_1} ) * x_2^{e_2} ... ) * x_n^{e_n},
+ * every sum taken left to right from its e = 0 term, powers by repeated
+ * multiplication from 1.0.  This fixes every rounding, so results are
+ * reproducible bit for bit on any IEEE machine.
+ *
+ * A pixel is on when f at its centre is finite and (Sec. 3.2, "the error at the
+ * centre achieves eps"):  PA_EQ: |f| <= eps;  PA_LE: f <= eps;  PA_LT: f < eps.
+ * With strict = 1 every "<=" becomes "<" (the test used by the paper's
+ * Appendix A code).  NaN and +-Inf turn the pixel off (Sec. 2.4).
+ *
+ * Bit-packed arrays (pa_array): axes in the order of `vars`, last axis fastest.
+ * Every last-axis row is packed LSB-first into ceil(res_last / 64) uint64 words
+ * (bit b of word w is pixel 64*w + b); unused high bits of the last word are 0.
+ * Rows follow each other in row-major order of the other axes.  A 0-dimensional
+ * array (no exposed variables: "does a solution exist") is one word, bit 0.
+ *
+ * Ownership: the caller allocates every pa_array's words on the context's
+ * device and keeps them alive until the stream work finishes; the library
+ * never frees them.  The context owns only its own scratch workspace.
+ *
+ * Errors: every call returns a pa_status; nothing is thrown across the ABI.
+ * pa_last_error(ctx) gives a message for the last failure on that context.
+ * Shapes and arguments are checked before any launch; a launch failure is
+ * reported by the call that made it; a fault inside a kernel surfaces at the
+ * next synchronisation of the stream.
+ *
+ * Concurrency: one context serves one stream at a time.  Two calls on the same
+ * context must be ordered on the device (same stream, or events) because they
+ * share the context's workspace.  Use one context per concurrent stream.
+ */
+#ifndef PA_H_
+#define PA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_MAX_DIM 8     /* ports per relation / axes per array */
+#define PA_MAX_DEGREE 16 /* total degree of a relation's polynomial */
+
+typedef enum {
+  PA_OK = 0,
+  PA_ERR_INVALID_ARG = 1, /* a null pointer, a bad size, inconsistent shapes */
+  PA_ERR_UNSUPPORTED = 2, /* valid input outside this build's limits */
+  PA_ERR_TOO_LARGE = 3,   /* an array or index would overflow 2^62 bits */
+  PA_ERR_OOM = 4,         /* the workspace could not be allocated */
+  PA_ERR_CUDA = 5,        /* a CUDA call failed; see pa_last_error */
+  PA_ERR_TIMEOUT = 6      /* a bounded device wait ran out */
+} pa_status;
+
+/* Target set S of a relation f(x) in S (Sec. 3.2, functionally-defined
+ * relations): {0}, (-inf, 0] or (-inf, 0). */
+typedef enum { PA_EQ = 0, PA_LE = 1, PA_LT = 2 } pa_kind;
+
+/* One variable's range [lo, hi) and resolution (Sec. 3.1, pack). lo < hi,
+ * both finite, res >= 2. */
+typedef struct {
+  double lo;
+  double hi;
+  int32_t res;
+} pa_axis;
+
+/* A polynomial relation over `arity` ports; port p reads variable vars[p].
+ * A variable may fill several ports (a loop in the wiring diagram, Sec. 3.1):
+ * the relation is then plotted on the diagonal.  `coeffs` is a HOST pointer to
+ * C(arity + degree, degree) doubles in graded lex order.  eps >= 0 is the
+ * tolerance; eps < 0 asks the library for a valid one (pa_valid_tolerance). */
+typedef struct {
+  int32_t arity;
+  int32_t vars[PA_MAX_DIM];
+  int32_t degree;
+  const double* coeffs;
+  int32_t kind;
+  double eps;
+} pa_relation;
+
+/* A bit-packed Boolean array on the device (layout above).  `words` holds
+ * pa_array_words(this) uint64 words.  vars are distinct. */
+typedef struct {
+  uint64_t* words;
+  int32_t ndim;
+  int32_t vars[PA_MAX_DIM];
+  int32_t res[PA_MAX_DIM];
+} pa_array;
+
+/* Contraction order of pa_solve_network.  Any order gives the same bits
+ * (Sec. 3.3, Thm. associative); only the time differs. */
+typedef enum {
+  PA_ORDER_GREEDY = 0, /* repeatedly join the pair with the smallest result */
+  PA_ORDER_GIVEN = 1,  /* join the pairs listed in pa_options.pairs */
+  PA_ORDER_LEFT = 2    /* fold the relations left to right */
+} pa_order;
+
+typedef struct {
+  int32_t strict;       /* 1: strict comparison (see above); 0: default */
+  int32_t order;        /* pa_order */
+  int32_t npairs;       /* PA_ORDER_GIVEN: nrel - 1 joins */
+  const int32_t* pairs; /* PA_ORDER_GIVEN: 2*npairs slot indices, host; slots
+                           0..nrel-1 are the plots, join t creates slot nrel+t */
+} pa_options;
+
+typedef struct {
+  double pixels_plotted;     /* sum over relations of the pixels evaluated */
+  double pixel_ops_dense;    /* sum over joins of r^Lambda (Sec. 3.5, naive cost) */
+  double words_or_executed;  /* 64-bit OR words the contraction kernels read */
+  int32_t n_plots;
+  int32_t n_joins;
+  int32_t n_reshapes;
+  int32_t n_launches;        /* kernels and memsets enqueued by the call */
+  int64_t peak_words;        /* largest intermediate array, words */
+  int64_t workspace_bytes;   /* workspace in use by the call */
+} pa_stats;
+
+typedef struct pa_ctx pa_ctx;
+
+/* Create a context on `device`.  workspace_cap bounds the scratch memory the
+ * context may hold (0: no bound).  Returns PA_ERR_CUDA when the device cannot
+ * be used (no GPU, wrong architecture). */
+pa_status pa_create(pa_ctx** ctx, int device, size_t workspace_cap);
+void pa_destroy(pa_ctx* ctx);
+const char* pa_last_error(const pa_ctx* ctx);
+/* Block the host until the work this context enqueued on `stream` is done and
+ * report any device-side error. */
+pa_status pa_sync(pa_ctx* ctx, void* stream);
+
+/* Kernel timing.  While enabled, every kernel (and memset) the context enqueues
+ * is bracketed by a pair of CUDA events on the same stream.  pa_profile_read
+ * waits for those events, adds the elapsed times up per kernel name and clears
+ * the record.  names receives up to max_kernels NUL-terminated names of at most
+ * 31 characters, 32 bytes apart; launches[k] and total_ms[k] the count and the
+ * summed milliseconds of kernel k; *nkernels the number of distinct kernels. */
+pa_status pa_profile_enable(pa_ctx* ctx, int32_t on);
+pa_status pa_profile_read(pa_ctx* ctx, int32_t max_kernels, char* names, int64_t* launches,
+                          double* total_ms, int32_t* nkernels);
+
+/* Number of uint64 words of a pa_array of this shape (host only, no GPU). */
+int64_t pa_array_words(int32_t ndim, const int32_t* res);
+
+/* A valid tolerance for `rel` on the box `axes` (indexed by variable id), Sec.
+ * 3.2 Eq. (continuity): eps with |f(x) - f(c)| <= eps whenever x lies in the
+ * pixel centred at c.  Computed on the host as
+ *   (1 + 2^-30) * sum_p S_p * delta_p / 2,
+ *   S_p = sum_e |c_e| e_p M_p^(e_p - 1) prod_{q != p} M_q^(e_q),  M_q = max(|lo_q|, |hi_q|),
+ * in a fixed order (ports ascending, monomials in graded lex order, factors left
+ * to right).  Host only, no GPU. */
+pa_status pa_valid_tolerance(const pa_relation* rel, const pa_axis* axes, int32_t nvars,
+                             double* eps_out);
+
+/* Plot one relation (Sec. 3.2, sample-in-center plot) into `out`, whose vars
+ * must be the relation's distinct variables in order of first appearance and
+ * whose res must match `axes`. */
+pa_status pa_plot(pa_ctx* ctx, const pa_relation* rel, const pa_axis* axes, int32_t nvars,
+                  int32_t strict, pa_array* out, void* stream);
+
+/* One two-array cluster (Sec. 3.5): out = Eq. (GAM) applied to A and B with the
+ * outer pack `keep`: out(e') = OR over the values of every variable of A or B
+ * not in keep of A(e_A) AND B(e_B).  out->vars must equal keep (distinct, each
+ * a variable of A or B); shared variables must have equal res.  A, B and out
+ * must not overlap. */
+pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t nkeep,
+                      const int32_t* keep, pa_array* out, void* stream);
+
+/* The whole method (Sec. 3.6): plot every relation, join the plots pairwise in
+ * the order chosen by opts->order, and leave the array over `exposed` (in that
+ * axis order) in `out`.  nexposed = 0 gives one bit: does the system have a
+ * solution pixel.  opts and stats may be NULL.  The order is planned on the
+ * host from the shapes alone, so the call never waits for the device. */
+pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,
+                           const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
+                           const pa_options* opts, pa_array* out, pa_stats* stats,
+                           void* stream);
+
+/* The join order pa_solve_network would use (host only, no GPU): writes
+ * 2*(nrel-1) slot indices into pairs_out (same numbering as pa_options.pairs). */
+pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const pa_relation* rels,
+                        int32_t nexposed, const int32_t* exposed, int32_t order,
+                        int32_t* pairs_out, double* pixel_ops_out, int64_t* peak_bits_out);
+
+/* Cost of a cluster tree (Sec. 3.5, cost polynomial evaluated at the given
+ * resolutions), host only.  Links 0..nlinks-1 have resolutions link_res.  Inner
+ * pack i (0..npacks-1) has pack_nports[i] ports wired to the links listed in
+ * pack_links (concatenated); the outer pack's ports are wired to outer_links.
+ * The tree is a list of clusters: cluster t joins join_nchildren[t] slots
+ * listed in join_children (concatenated); slots 0..npacks-1 are the packs and
+ * cluster t creates slot npacks + t; the last cluster is the root.  A slot's
+ * intermediate pack is the set of its links that also touch something outside
+ * it (another pack or the outer pack).  A cluster costs r^(links of its
+ * children's packs); the root also counts the outer pack's links.  Writes the serial cost (sum over the clusters) and the
+ * parallel cost (a cluster's cost plus the largest parallel cost among its
+ * children). */
+pa_status pa_tree_cost(int32_t nlinks, const double* link_res, int32_t npacks,
+                       const int32_t* pack_nports, const int32_t* pack_links,
+                       int32_t nouter, const int32_t* outer_links, int32_t njoins,
+                       const int32_t* join_nchildren, const int32_t* join_children,
+                       double* serial_cost, double* parallel_cost);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H_ */

@@ -344,7 +344,7 @@ int or_contract_pair(int nx, const int* xvars, const uint8_t* X, int ny, const i
     for (int k = 0; k < nsum; ++k) cnt[k] = 0;
     uint8_t acc = 0;
     for (int64_t s = 0; s < sum_size; ++s) {
-      acc = X[xi] & Y[yi];
+      acc = X[xi] && Y[yi];  /* Y is read only where X is on */
       if (acc) break;
       /* next value of the summed variables, last one fastest */
       for (int k = nsum - 1; k >= 0; --k) {

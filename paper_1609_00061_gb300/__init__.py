@@ -1,0 +1,280 @@
+"""GB300 pixel array engine: Python binding of the C interface in include/pa.h.
+
+The pixel array method (Spivak, Dobson, Kumari, Wu, arXiv 1609.00061) plots
+every relation of a system as a Boolean pixel array and joins the plots by
+Boolean generalized array multiplication until only the exposed variables are
+left.  All of that runs in the CUDA kernels of libpa_gb300.so; this module only
+marshals arguments (torch provides device memory and streams).
+
+Functions keep the C names:
+    pa_create, pa_valid_tolerance, pa_plot, pa_contract, pa_solve_network,
+    pa_plan_order, pa_tree_cost, pa_array_words
+and ``Engine`` bundles them for everyday use.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+from ._native import PaArray, PaAxis, PaOptions, PaRelation, PaStats
+
+PA_OK = 0
+STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
+          4: "PA_ERR_OOM", 5: "PA_ERR_CUDA", 6: "PA_ERR_TIMEOUT"}
+ORDERS = {"greedy": 0, "given": 1, "left": 2}
+
+
+class PaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _lib():
+    return _native.load()
+
+
+def _check(status, ctx=None):
+    if status != PA_OK:
+        msg = _lib().pa_last_error(ctx).decode() if ctx else ""
+        raise PaError(status, msg)
+
+
+# ------------------------------------------------------------- marshalling
+def _axes(axes):
+    arr = (PaAxis * max(1, len(axes)))()
+    for i, (lo, hi, res) in enumerate(axes):
+        arr[i].lo, arr[i].hi, arr[i].res = float(lo), float(hi), int(res)
+    return arr
+
+
+def _relations(rels):
+    arr = (PaRelation * len(rels))()
+    keep = []
+    for i, r in enumerate(rels):
+        c = np.ascontiguousarray(r.coeffs, dtype=np.float64)
+        keep.append(c)
+        arr[i].arity = len(r.vars)
+        for p, v in enumerate(r.vars):
+            arr[i].vars[p] = int(v)
+        arr[i].degree = int(r.degree)
+        arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].kind = int(r.kind)
+        arr[i].eps = float(r.eps)
+    return arr, keep
+
+
+def _i32(vals):
+    vals = list(vals)
+    a = (ctypes.c_int32 * max(1, len(vals)))(*[int(v) for v in vals])
+    return a
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pa_array_words(res) -> int:
+    res = list(res)
+    return int(_lib().pa_array_words(len(res), _i32(res)))
+
+
+@dataclass
+class BitArray:
+    """A bit-packed Boolean array on the GPU (layout of include/pa.h)."""
+    words: "object"       # torch.int64 CUDA tensor holding the uint64 words
+    vars: tuple
+    res: tuple
+
+    @staticmethod
+    def empty(vars, res, device=0):
+        import torch
+        n = pa_array_words(res)
+        return BitArray(torch.empty(n, dtype=torch.int64, device=f"cuda:{device}"),
+                        tuple(int(v) for v in vars), tuple(int(r) for r in res))
+
+    def c(self) -> PaArray:
+        a = PaArray()
+        a.words = ctypes.c_void_p(self.words.data_ptr())
+        a.ndim = len(self.vars)
+        for i, (v, r) in enumerate(zip(self.vars, self.res)):
+            a.vars[i] = v
+            a.res[i] = r
+        return a
+
+    def to_numpy(self) -> np.ndarray:
+        """Unpack to one uint8 per pixel (numpy shape = res)."""
+        w = self.words.detach().cpu().numpy().view(np.uint64)
+        if len(self.res) == 0:
+            return np.array(int(w[0]) & 1, dtype=np.uint8)
+        rw = (self.res[-1] + 63) // 64
+        rows = w.reshape(-1, rw)
+        bits = np.unpackbits(rows.view(np.uint8).reshape(rows.shape[0], rw * 8), axis=1,
+                             bitorder="little")[:, :self.res[-1]]
+        return bits.reshape(self.res)
+
+    def padding_clean(self) -> bool:
+        """True when every unused high bit of every row is zero."""
+        if len(self.res) == 0:
+            return (int(self.words[0].item()) & ~1) == 0
+        r = self.res[-1]
+        if r % 64 == 0:
+            return True
+        rw = (r + 63) // 64
+        w = self.words.detach().cpu().numpy().view(np.uint64).reshape(-1, rw)[:, -1]
+        mask = np.uint64(~((1 << (r % 64)) - 1) & ((1 << 64) - 1))
+        return bool(np.all((w & mask) == 0))
+
+
+# ------------------------------------------------------------- C entry points
+def pa_create(device: int = 0, workspace_cap: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(_lib().pa_create(ctypes.byref(ctx), device, workspace_cap))
+    return ctx
+
+
+def pa_valid_tolerance(rel, axes) -> float:
+    r, keep = _relations([rel])
+    out = ctypes.c_double()
+    _check(_lib().pa_valid_tolerance(r, _axes(axes), len(axes), ctypes.byref(out)))
+    return out.value
+
+
+def pa_plot(ctx, rel, axes, out: BitArray, strict=False, stream=None):
+    r, keep = _relations([rel])
+    o = out.c()
+    _check(_lib().pa_plot(ctx, r, _axes(axes), len(axes), int(bool(strict)), ctypes.byref(o),
+                          _stream_ptr(stream)), ctx)
+    return out
+
+
+def pa_contract(ctx, A: BitArray, B: BitArray, keep, out: BitArray, stream=None):
+    a, b, o = A.c(), B.c(), out.c()
+    _check(_lib().pa_contract(ctx, ctypes.byref(a), ctypes.byref(b), len(keep), _i32(keep),
+                              ctypes.byref(o), _stream_ptr(stream)), ctx)
+    return out
+
+
+def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pairs=None,
+                     strict=False, stream=None) -> dict:
+    r, keep = _relations(rels)
+    opts = PaOptions()
+    opts.strict = int(bool(strict))
+    opts.order = ORDERS[order] if isinstance(order, str) else int(order)
+    pr = None
+    if pairs is not None:
+        flat = [int(v) for p in pairs for v in p]
+        pr = _i32(flat)
+        opts.npairs = len(pairs)
+        opts.pairs = ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32))
+    st = PaStats()
+    o = out.c()
+    _check(_lib().pa_solve_network(ctx, len(axes), _axes(axes), len(rels), r, len(exposed),
+                                   _i32(exposed), ctypes.byref(opts), ctypes.byref(o),
+                                   ctypes.byref(st), _stream_ptr(stream)), ctx)
+    return st.as_dict()
+
+
+def pa_plan_order(axes, rels, exposed, order="greedy"):
+    """Join order (list of slot pairs), dense pixel-op count and peak bits; host only."""
+    r, keep = _relations(rels)
+    n = len(rels)
+    pairs = (ctypes.c_int32 * max(1, 2 * (n - 1)))()
+    ops = ctypes.c_double()
+    peak = ctypes.c_int64()
+    _check(_lib().pa_plan_order(len(axes), _axes(axes), n, r, len(exposed), _i32(exposed),
+                                ORDERS[order], pairs, ctypes.byref(ops), ctypes.byref(peak)))
+    return [(pairs[2 * t], pairs[2 * t + 1]) for t in range(n - 1)], ops.value, peak.value
+
+
+def pa_tree_cost(link_res, packs, outer, clusters):
+    """Serial and parallel cost of a cluster tree (host only).
+
+    packs: list of link-index lists; outer: link indices of the outer pack;
+    clusters: list of slot lists (slots 0..len(packs)-1 are packs, cluster t
+    creates slot len(packs)+t)."""
+    lr = (ctypes.c_double * max(1, len(link_res)))(*[float(v) for v in link_res])
+    nports = _i32([len(p) for p in packs])
+    plinks = _i32([l for p in packs for l in p])
+    s, p = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().pa_tree_cost(len(link_res), lr, len(packs), nports, plinks, len(outer),
+                               _i32(outer), len(clusters), _i32([len(c) for c in clusters]),
+                               _i32([x for c in clusters for x in c]), ctypes.byref(s),
+                               ctypes.byref(p)))
+    return s.value, p.value
+
+
+def pa_profile_enable(ctx, on=True):
+    _check(_lib().pa_profile_enable(ctx, int(bool(on))), ctx)
+
+
+def pa_profile_read(ctx) -> dict:
+    """{kernel name: (launches, total ms)} since the last read; waits for the events."""
+    cap = 64
+    names = ctypes.create_string_buffer(32 * cap)
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = ctypes.c_int32()
+    _check(_lib().pa_profile_read(ctx, cap, names, launches, ms, ctypes.byref(n)), ctx)
+    out = {}
+    for k in range(min(n.value, cap)):
+        nm = names.raw[32 * k:32 * k + 32].split(b"\0")[0].decode()
+        out[nm] = (int(launches[k]), float(ms[k]))
+    return out
+
+
+def pa_sync(ctx, stream=None):
+    _check(_lib().pa_sync(ctx, _stream_ptr(stream)), ctx)
+
+
+# ------------------------------------------------------------------ Engine
+class Engine:
+    """One context on one GPU; allocates outputs as torch tensors."""
+
+    def __init__(self, device: int = 0, workspace_cap: int = 0):
+        self.device = device
+        self.ctx = pa_create(device, workspace_cap)
+
+    def close(self):
+        if self.ctx:
+            _lib().pa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plot(self, rel, axes, strict=False, stream=None) -> BitArray:
+        dv = []
+        for v in rel.vars:
+            if v not in dv:
+                dv.append(v)
+        out = BitArray.empty(dv, [axes[v][2] for v in dv], self.device)
+        return pa_plot(self.ctx, rel, axes, out, strict, stream)
+
+    def contract(self, A: BitArray, B: BitArray, keep, stream=None) -> BitArray:
+        res = {}
+        for v, r in zip(A.vars + B.vars, A.res + B.res):
+            res[v] = r
+        out = BitArray.empty(keep, [res[v] for v in keep], self.device)
+        return pa_contract(self.ctx, A, B, keep, out, stream)
+
+    def solve(self, system, order="greedy", pairs=None, strict=False, stream=None, out=None):
+        """Solve a workloads.System; returns (BitArray over system.exposed, stats)."""
+        if out is None:
+            out = BitArray.empty(system.exposed, [system.axes[v][2] for v in system.exposed],
+                                 self.device)
+        st = pa_solve_network(self.ctx, system.axes, system.rels, system.exposed, out, order,
+                              pairs, strict, stream)
+        return out, st
+
+    def sync(self, stream=None):
+        pa_sync(self.ctx, stream)

@@ -1,0 +1,154 @@
+"""Build and load the engine's shared library (libpa_gb300.so) and declare its C ABI.
+
+The library is compiled in-tree for sm_103a only.  There is no fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
+_ROOT = os.path.dirname(_HERE)
+INCLUDE = os.path.join(_ROOT, "include")
+
+CU_SOURCES = ["api.cu", "plot.cu", "contract.cu"]
+CPP_SOURCES = ["planner.cpp"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _sources():
+    return [os.path.join(_CSRC, f) for f in CU_SOURCES + CPP_SOURCES] + \
+        [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".h")] + \
+        [os.path.join(INCLUDE, "pa.h")]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit (in parallel) and link libpa_gb300.so."""
+    srcs = _sources()
+    if (not force and os.path.exists(LIB_PATH)
+            and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(s) for s in srcs)):
+        return LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    nvcc = _nvcc()
+    common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", f"-I{INCLUDE}",
+              "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math"]
+    jobs = []
+    for f in CU_SOURCES:
+        obj = os.path.join(_BUILD, f.replace(".cu", ".o"))
+        jobs.append([nvcc, *ARCH, *common, "-c", os.path.join(_CSRC, f), "-o", obj])
+    for f in CPP_SOURCES:
+        obj = os.path.join(_BUILD, f.replace(".cpp", ".o"))
+        jobs.append([nvcc, *common, "-x", "c++", "-c", os.path.join(_CSRC, f), "-o", obj])
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("build failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        if verbose and (r.stdout or r.stderr):
+            print(r.stdout + r.stderr)
+
+    with ThreadPoolExecutor(max_workers=len(jobs)) as pool:
+        list(pool.map(run, jobs))
+    objs = [j[-1] for j in jobs]
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ----------------------------------------------------------------- C structs
+MAX_DIM = 8
+c_i32, c_i64, c_f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class PaAxis(ctypes.Structure):
+    _fields_ = [("lo", c_f64), ("hi", c_f64), ("res", c_i32)]
+
+
+class PaRelation(ctypes.Structure):
+    _fields_ = [("arity", c_i32), ("vars", c_i32 * MAX_DIM), ("degree", c_i32),
+                ("coeffs", ctypes.POINTER(c_f64)), ("kind", c_i32), ("eps", c_f64)]
+
+
+class PaArray(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_void_p), ("ndim", c_i32), ("vars", c_i32 * MAX_DIM),
+                ("res", c_i32 * MAX_DIM)]
+
+
+class PaOptions(ctypes.Structure):
+    _fields_ = [("strict", c_i32), ("order", c_i32), ("npairs", c_i32),
+                ("pairs", ctypes.POINTER(c_i32))]
+
+
+class PaStats(ctypes.Structure):
+    _fields_ = [("pixels_plotted", c_f64), ("pixel_ops_dense", c_f64),
+                ("words_or_executed", c_f64), ("n_plots", c_i32), ("n_joins", c_i32),
+                ("n_reshapes", c_i32), ("n_launches", c_i32), ("peak_words", c_i64),
+                ("workspace_bytes", c_i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_words",
+           "pa_profile_enable", "pa_profile_read",
+           "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_plan_order",
+           "pa_tree_cost"]
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libpa_gb300.so (building it first when allowed).  Raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"{LIB_PATH} is missing; run __graft_entry__.build()")
+        build()
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.pa_create.argtypes = [P(vp), ctypes.c_int, ctypes.c_size_t]
+    lib.pa_create.restype = c_i32
+    lib.pa_destroy.argtypes = [vp]
+    lib.pa_destroy.restype = None
+    lib.pa_last_error.argtypes = [vp]
+    lib.pa_last_error.restype = ctypes.c_char_p
+    lib.pa_sync.argtypes = [vp, vp]
+    lib.pa_sync.restype = c_i32
+    lib.pa_profile_enable.argtypes = [vp, c_i32]
+    lib.pa_profile_enable.restype = c_i32
+    lib.pa_profile_read.argtypes = [vp, c_i32, ctypes.c_char_p, P(c_i64), P(c_f64), P(c_i32)]
+    lib.pa_profile_read.restype = c_i32
+    lib.pa_array_words.argtypes = [c_i32, P(c_i32)]
+    lib.pa_array_words.restype = c_i64
+    lib.pa_valid_tolerance.argtypes = [P(PaRelation), P(PaAxis), c_i32, P(c_f64)]
+    lib.pa_valid_tolerance.restype = c_i32
+    lib.pa_plot.argtypes = [vp, P(PaRelation), P(PaAxis), c_i32, c_i32, P(PaArray), vp]
+    lib.pa_plot.restype = c_i32
+    lib.pa_contract.argtypes = [vp, P(PaArray), P(PaArray), c_i32, P(c_i32), P(PaArray), vp]
+    lib.pa_contract.restype = c_i32
+    lib.pa_solve_network.argtypes = [vp, c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32),
+                                     P(PaOptions), P(PaArray), P(PaStats), vp]
+    lib.pa_solve_network.restype = c_i32
+    lib.pa_plan_order.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32), c_i32,
+                                  P(c_i32), P(c_f64), P(c_i64)]
+    lib.pa_plan_order.restype = c_i32
+    lib.pa_tree_cost.argtypes = [c_i32, P(c_f64), c_i32, P(c_i32), P(c_i32), c_i32, P(c_i32),
+                                 c_i32, P(c_i32), P(c_i32), P(c_f64), P(c_f64)]
+    lib.pa_tree_cost.restype = c_i32
+    _lib = lib
+    return lib

@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of the pixel array
+// engine.  Nothing here is part of the public C interface (include/pa.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+constexpr int kMaxDim = PA_MAX_DIM;
+constexpr int kMaxDeg = PA_MAX_DEGREE;
+
+// ------------------------------------------------------------------ plotting
+// One relation to plot.  Coefficients are in "nest order": the order in which
+// the nested evaluation visits the monomials (last port outermost, every
+// exponent ascending), so the device reads them front to back.
+struct PlotJob {
+  const double* coeffs;             // device, nest order
+  uint64_t* out;                    // device, pa_array layout
+  const double* x64[kMaxDim];       // per port: FP64 pixel centres of its variable
+  const float* x32_last;            // FP32 copies of the last port's centres
+  int64_t nrows;                    // rows = product of all but the last array axis
+  int64_t row_words;                // ceil(res_last / 64)
+  int64_t tile0;                    // first block of this job in the launch
+  int32_t rows_per_tile;
+  int32_t arity, degree, kind, strict;
+  int32_t hoisted;                  // 1: the last port is the last array axis, used once
+  int32_t ndim;                     // array axes (distinct variables)
+  int32_t res[kMaxDim];             // array axis resolutions
+  int32_t port_axis[kMaxDim];       // port -> array axis
+  double eps;
+  float eps32;                      // eps rounded to FP32
+  float kfac;                       // FP32 filter: error bound factor on sum |g_j y^j|
+  float abs_margin;                 // FP32 filter: margin for eps rounding / underflow
+};
+
+// Centre tables: x64[off_v + i] = lo_v + ((double)i + 0.5) * ((hi_v - lo_v) / res_v).
+struct AxisTableJob {
+  double lo, hi;
+  int32_t res;
+  int64_t off;
+};
+
+void launch_axis_tables(const AxisTableJob* d_jobs, int njobs, int64_t total, double* x64,
+                        float* x32, cudaStream_t s);
+void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
+                 int max_degree, cudaStream_t s);
+
+// ------------------------------------------------------------- bit arrays
+// A bit-packed array with `inner` trailing axes flattened into packed rows:
+// rowlen = prod(res[ndim-inner..]), row_words = ceil(rowlen / 64),
+// nrows = prod(res[..ndim-inner]).  The public pa_array layout is inner = 1
+// (inner = 0 for ndim = 0).
+struct BitArr {
+  uint64_t* w = nullptr;
+  int ndim = 0;
+  int inner = 0;
+  int vars[2 * kMaxDim] = {};
+  int64_t res[2 * kMaxDim] = {};
+  int64_t rowlen() const {
+    int64_t r = 1;
+    for (int a = ndim - inner; a < ndim; ++a) r *= res[a];
+    return r;
+  }
+  int64_t row_words() const { return (rowlen() + 63) / 64; }
+  int64_t nrows() const {
+    int64_t r = 1;
+    for (int a = 0; a < ndim - inner; ++a) r *= res[a];
+    return r;
+  }
+  int64_t words() const { return nrows() * row_words(); }
+  int64_t bits() const { return nrows() * rowlen(); }
+};
+
+// General gather: out bit (axes of `out`) = OR over the reduced input axes of
+// the input bit with the same values of the shared axes.  out_from_in[a] is the
+// input axis feeding output axis a (-1: broadcast along a).
+struct ReshapeDesc {
+  const uint64_t* in;
+  uint64_t* out;
+  int64_t out_nrows, out_row_words, out_rowlen;
+  int32_t out_ndim, out_inner;
+  int64_t out_res[2 * kMaxDim];
+  int64_t row_stride[2 * kMaxDim];  // per output axis: input row-index stride
+  int64_t col_stride[2 * kMaxDim];  // per output axis: input column (bit) stride
+  int32_t nred;
+  int64_t red_res[2 * kMaxDim];
+  int64_t red_row_stride[2 * kMaxDim];
+  int64_t red_col_stride[2 * kMaxDim];
+  int64_t in_row_words;
+  int32_t word_mode;  // 1: output columns map 1:1 onto input columns (copy words)
+};
+void launch_reshape(const ReshapeDesc& d, cudaStream_t s);
+
+// C[b*M + m, :] |= B[b*K + k, :] for every set bit k of A[b*M + m, :].
+struct RowOrDesc {
+  const uint64_t* A;
+  const uint64_t* B;
+  uint64_t* C;
+  int64_t nbatch, M, K, Nw;   // Nw = words per B / C row
+  int64_t a_row_words;        // = ceil(K / 64)
+  int64_t kchunk_words;       // A words per task
+  int64_t nkchunks, nnchunks;
+  int32_t atomic;             // 1: C pre-zeroed, results OR-ed in atomically
+};
+void launch_rowor(const RowOrDesc& d, cudaStream_t s);
+// words of one output row that one row-OR task covers (its n-chunk width)
+int64_t rowor_chunk_words(int64_t Nw);
+// cudaSuccess when this build holds kernel code the current device can run
+cudaError_t probe_kernel_image();
+void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
+
+// ----------------------------------------------------------- host helpers
+int64_t coeff_count(int n, int degree);
+// graded lex rank of every monomial in nest order (host)
+std::vector<int64_t> nest_order(int n, int degree);
+double valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
+                       const double* hi, const int32_t* res);
+
+}  // namespace pa

@@ -1,0 +1,290 @@
+// Host-side planning for the pixel array engine: polynomial bookkeeping, the
+// valid tolerance of Sec. 3.2, the join order of Sec. 3.5 and cluster-tree
+// costs.  Built with -ffp-contract=off so every double operation rounds once.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pa_internal.h"
+#include "planner.h"
+
+namespace pa {
+
+int64_t coeff_count(int n, int degree) {
+  // C(n + degree, degree)
+  int64_t r = 1;
+  for (int i = 1; i <= degree; ++i) r = r * (n + i) / i;
+  return r;
+}
+
+// Every exponent tuple of n variables with total degree <= degree, in graded
+// lex order (degree ascending, then descending lexicographic).
+static void graded_lex(int n, int degree, std::vector<std::vector<int>>& out) {
+  out.clear();
+  std::vector<int> e(n, 0);
+  // recursive fill of position i with the remaining sum, largest value first
+  struct Rec {
+    static void go(int i, int n, int left, std::vector<int>& e, std::vector<std::vector<int>>& out) {
+      if (i == n - 1) {
+        e[i] = left;
+        out.push_back(e);
+        return;
+      }
+      for (int v = left; v >= 0; --v) {
+        e[i] = v;
+        go(i + 1, n, left - v, e, out);
+      }
+    }
+  };
+  for (int t = 0; t <= degree; ++t) {
+    if (n == 0) {
+      if (t == 0) out.push_back(e);
+      continue;
+    }
+    Rec::go(0, n, t, e, out);
+  }
+}
+
+static int64_t tuple_key(const std::vector<int>& e, int degree) {
+  int64_t k = 0;
+  for (int v : e) k = k * (degree + 1) + v;
+  return k;
+}
+
+std::vector<int64_t> nest_order(int n, int degree) {
+  std::vector<std::vector<int>> gl;
+  graded_lex(n, degree, gl);
+  // rank lookup by key
+  std::vector<std::pair<int64_t, int64_t>> keyrank;
+  keyrank.reserve(gl.size());
+  for (size_t i = 0; i < gl.size(); ++i) keyrank.push_back({tuple_key(gl[i], degree), (int64_t)i});
+  std::sort(keyrank.begin(), keyrank.end());
+  std::vector<int64_t> order;
+  order.reserve(gl.size());
+  std::vector<int> e(n, 0);
+  // visit(k, rem): the last variable outermost, each exponent ascending
+  struct Visit {
+    static void go(int k, int rem, int degree, std::vector<int>& e,
+                   const std::vector<std::pair<int64_t, int64_t>>& kr, std::vector<int64_t>& order) {
+      if (k < 0) {
+        int64_t key = tuple_key(e, degree);
+        auto it = std::lower_bound(kr.begin(), kr.end(), std::make_pair(key, (int64_t)-1));
+        order.push_back(it->second);
+        return;
+      }
+      for (int v = 0; v <= rem; ++v) {
+        e[k] = v;
+        go(k - 1, rem - v, degree, e, kr, order);
+      }
+      e[k] = 0;
+    }
+  };
+  Visit::go(n - 1, degree, degree, e, keyrank, order);
+  return order;
+}
+
+double valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
+                       const double* hi, const int32_t* res) {
+  std::vector<std::vector<int>> gl;
+  graded_lex(n, degree, gl);
+  double M[kMaxDim];
+  for (int q = 0; q < n; ++q) M[q] = fmax(fabs(lo[q]), fabs(hi[q]));
+  double total = 0.0;
+  for (int p = 0; p < n; ++p) {
+    double S = 0.0;
+    for (size_t m = 0; m < gl.size(); ++m) {
+      const std::vector<int>& e = gl[m];
+      if (e[p] == 0) continue;
+      double t = fabs(coeffs[m]) * (double)e[p];
+      double pp = 1.0;
+      for (int k = 1; k < e[p]; ++k) pp = pp * M[p];
+      t = t * pp;
+      for (int q = 0; q < n; ++q) {
+        if (q == p) continue;
+        double pq = 1.0;
+        for (int k = 0; k < e[q]; ++k) pq = pq * M[q];
+        t = t * pq;
+      }
+      S = S + t;
+    }
+    double delta = (hi[p] - lo[p]) / (double)res[p];
+    total = total + S * (delta * 0.5);
+  }
+  return total * (1.0 + 0x1p-30);
+}
+
+// ------------------------------------------------------------- join order
+static double set_size(const std::vector<int>& vars, const std::vector<double>& vres) {
+  double s = 1.0;
+  for (int v : vars) s *= vres[v];
+  return s;
+}
+
+static std::vector<int> set_union(const std::vector<int>& a, const std::vector<int>& b) {
+  std::vector<int> u = a;
+  for (int v : b)
+    if (std::find(u.begin(), u.end(), v) == u.end()) u.push_back(v);
+  return u;
+}
+
+Plan plan_joins(int nvars, const std::vector<double>& vres,
+                const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
+                int order, const int32_t* given_pairs) {
+  Plan plan;
+  int nrel = (int)rel_vars.size();
+  // live slots: slot id -> variable set
+  std::vector<std::vector<int>> slot_vars;
+  for (auto& rv : rel_vars) {
+    std::vector<int> d;
+    for (int v : rv)
+      if (std::find(d.begin(), d.end(), v) == d.end()) d.push_back(v);
+    slot_vars.push_back(d);
+  }
+  std::vector<int> live;
+  for (int i = 0; i < nrel; ++i) live.push_back(i);
+  (void)nvars;
+  auto needed_outside = [&](const std::vector<int>& skip) {
+    std::vector<int> need = exposed;
+    for (int s : live) {
+      if (std::find(skip.begin(), skip.end(), s) != skip.end()) continue;
+      need = set_union(need, slot_vars[s]);
+    }
+    return need;
+  };
+  auto keep_of = [&](int a, int b) {
+    std::vector<int> u = set_union(slot_vars[a], slot_vars[b]);
+    std::vector<int> need = needed_outside({a, b});
+    std::vector<int> k;
+    for (int v : u)
+      if (std::find(need.begin(), need.end(), v) != need.end()) k.push_back(v);
+    return k;
+  };
+  for (int t = 0; t < nrel - 1; ++t) {
+    int a = -1, b = -1;
+    if (order == PA_ORDER_GIVEN) {
+      a = given_pairs[2 * t];
+      b = given_pairs[2 * t + 1];
+    } else if (order == PA_ORDER_LEFT) {
+      a = live[0];
+      b = live[1];
+    } else {
+      double best_size = 0, best_cost = 0;
+      for (size_t i = 0; i < live.size(); ++i)
+        for (size_t j = i + 1; j < live.size(); ++j) {
+          int x = live[i], y = live[j];
+          double size = set_size(keep_of(x, y), vres);
+          double cost = set_size(set_union(slot_vars[x], slot_vars[y]), vres);
+          if (a < 0 || size < best_size || (size == best_size && cost < best_cost)) {
+            a = x;
+            b = y;
+            best_size = size;
+            best_cost = cost;
+          }
+        }
+    }
+    Join jn;
+    jn.a = a;
+    jn.b = b;
+    jn.keep = keep_of(a, b);
+    jn.cost = set_size(set_union(slot_vars[a], slot_vars[b]), vres);
+    plan.joins.push_back(jn);
+    plan.pixel_ops += jn.cost;
+    plan.peak_bits = std::max(plan.peak_bits, set_size(jn.keep, vres));
+    int id = nrel + t;
+    slot_vars.push_back(jn.keep);
+    live.erase(std::find(live.begin(), live.end(), a));
+    live.erase(std::find(live.begin(), live.end(), b));
+    live.insert(live.begin(), id);
+    // keep the running product first so PA_ORDER_LEFT folds left to right
+  }
+  plan.root = live.empty() ? -1 : live[0];
+  return plan;
+}
+
+bool plan_valid_given(int nrel, int npairs, const int32_t* pairs) {
+  if (npairs != nrel - 1 || (nrel > 1 && pairs == nullptr)) return false;
+  std::vector<int> used(2 * nrel, 0);
+  for (int t = 0; t < npairs; ++t) {
+    int a = pairs[2 * t], b = pairs[2 * t + 1];
+    int limit = nrel + t;
+    if (a < 0 || b < 0 || a >= limit || b >= limit || a == b) return false;
+    if (used[a] || used[b]) return false;
+    used[a] = used[b] = 1;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ tree cost
+pa_status tree_cost(int32_t nlinks, const double* link_res, int32_t npacks,
+                    const int32_t* pack_nports, const int32_t* pack_links, int32_t nouter,
+                    const int32_t* outer_links, int32_t njoins, const int32_t* join_nchildren,
+                    const int32_t* join_children, double* serial, double* parallel) {
+  if (nlinks < 0 || npacks < 1 || njoins < 0 || !serial || !parallel) return PA_ERR_INVALID_ARG;
+  int nslots = npacks + njoins;
+  // members[s]: packs inside slot s; links[s]: links touched by slot s
+  std::vector<std::vector<int>> members(nslots);
+  std::vector<std::vector<int>> pack_link_list(npacks);
+  int off = 0;
+  for (int i = 0; i < npacks; ++i) {
+    for (int j = 0; j < pack_nports[i]; ++j) {
+      int l = pack_links[off + j];
+      if (l < 0 || l >= nlinks) return PA_ERR_INVALID_ARG;
+      pack_link_list[i].push_back(l);
+    }
+    off += pack_nports[i];
+    members[i].push_back(i);
+  }
+  std::vector<double> pcost(nslots, 0.0);
+  double total = 0.0;
+  int coff = 0;
+  // intermediate pack of a slot: its links that touch a pack outside it or the outer pack
+  auto inter_pack = [&](int s) {
+    std::vector<int> inside(npacks, 0);
+    for (int p : members[s]) inside[p] = 1;
+    std::vector<int> q;
+    for (int p : members[s])
+      for (int l : pack_link_list[p]) {
+        if (std::find(q.begin(), q.end(), l) != q.end()) continue;
+        bool outside = false;
+        for (int j = 0; j < nouter && !outside; ++j) outside = (outer_links[j] == l);
+        for (int p2 = 0; p2 < npacks && !outside; ++p2) {
+          if (inside[p2]) continue;
+          outside = std::find(pack_link_list[p2].begin(), pack_link_list[p2].end(), l) !=
+                    pack_link_list[p2].end();
+        }
+        if (outside) q.push_back(l);
+      }
+    return q;
+  };
+  for (int t = 0; t < njoins; ++t) {
+    int s = npacks + t;
+    std::vector<int> links;
+    double below = 0.0;
+    for (int c = 0; c < join_nchildren[t]; ++c) {
+      int ch = join_children[coff + c];
+      if (ch < 0 || ch >= s) return PA_ERR_INVALID_ARG;
+      for (int p : members[ch]) members[s].push_back(p);
+      std::vector<int> q = (ch < npacks) ? pack_link_list[ch] : inter_pack(ch);
+      links = set_union(links, q);
+      below = std::max(below, pcost[ch]);
+    }
+    coff += join_nchildren[t];
+    // the root is the exterior diagram of the last clustering: its links also
+    // include the outer pack's (Sec. 3.5, C-factorization)
+    if (t == njoins - 1)
+      for (int j = 0; j < nouter; ++j)
+        if (std::find(links.begin(), links.end(), outer_links[j]) == links.end())
+          links.push_back(outer_links[j]);
+    double c = 1.0;
+    for (int l : links) c *= link_res[l];
+    total += c;
+    pcost[s] = c + below;
+  }
+  *serial = total;
+  *parallel = njoins ? pcost[nslots - 1] : 0.0;
+  return PA_OK;
+}
+
+}  // namespace pa
