@@ -28,6 +28,7 @@ struct pa_ctx {
   bool stage_pending = false;
   std::string err;
   // kernel timing (pa_profile_enable)
+  int* d_err = nullptr;  // device error word written by bounded waits
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
@@ -359,23 +360,11 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
   for (int v : ch.K) d.K *= vres[v];
   d.Nw = Bm.row_words();
   d.a_row_words = Am.row_words();
-  const int64_t chunk = rowor_chunk_words(d.Nw);
-  d.nnchunks = (d.Nw + chunk - 1) / chunk;
-  // split K until there are enough tasks to fill the GPU
-  const int64_t rows = d.nbatch * d.M;
-  const int64_t want_tasks = 152 * 64 * std::max<int64_t>(1, 32 / std::min<int64_t>(32, chunk));
-  d.nkchunks = 1;
-  if (rows * d.nnchunks < want_tasks && d.a_row_words > 1) {
-    d.nkchunks = std::min<int64_t>(d.a_row_words, (want_tasks + rows * d.nnchunks - 1) /
-                                                     (rows * d.nnchunks));
-    d.nkchunks = std::max<int64_t>(1, std::min<int64_t>(d.nkchunks, d.a_row_words / 4 + 1));
-  }
-  d.kchunk_words = (d.a_row_words + d.nkchunks - 1) / d.nkchunks;
-  d.nkchunks = (d.a_row_words + d.kchunk_words - 1) / d.kchunk_words;
-  d.atomic = d.nkchunks > 1 ? 1 : 0;
+  d.err = ex.ctx->d_err;
+  rowor_plan(d);
   if (d.atomic) ex.memset0(C.w, C.words());
   ex.before("rowor_kernel");
-  if (!ex.dry) launch_rowor(d, ex.s);
+  if (!ex.dry) ex.check(launch_rowor(d, ex.s), "rowor_kernel");
   ex.launched("rowor_kernel");
   ex.st.peak_words = std::max<int64_t>(ex.st.peak_words, C.words());
   return C;
@@ -464,7 +453,7 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
   std::vector<char> blob;
   std::vector<size_t> coeff_off(nrel);
   int64_t tiles = 0;
-  int max_rows = 1, max_deg = 0;
+  int max_rows = 1, max_deg = 0, common_deg = rels[0].degree;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = rels[i];
     std::vector<int> dv = distinct_vars(r);
@@ -500,11 +489,12 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
     J.hoisted = (a.ndim == r.arity) ? 1 : 0;
     J.nrows = a.nrows();
     J.row_words = a.row_words();
-    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, 256 / J.row_words));
+    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, 512 / J.row_words));
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
     max_deg = std::max(max_deg, r.degree);
+    if (r.degree != common_deg) common_deg = -1;
     const double eps = relation_eps(r, axes);
     J.eps = eps;
     J.eps32 = (float)eps;
@@ -541,7 +531,7 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
   ex.before("plot_kernel");
   if (!ex.dry) {
     launch_plot(reinterpret_cast<const PlotJob*>(dblob + jobs_off), nrel, tiles, max_rows,
-                max_deg, ex.s);
+                max_deg, common_deg, ex.s);
   }
   ex.launched("plot_kernel");
   return plots;
@@ -655,7 +645,12 @@ pa_status pa_create(pa_ctx** out, int device, size_t workspace_cap) {
   pa_ctx* ctx = new pa_ctx();
   ctx->device = device;
   ctx->cap = workspace_cap;
-  if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_err), sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
     return PA_ERR_CUDA;
   }
@@ -668,6 +663,7 @@ void pa_destroy(pa_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_done);
   if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -722,6 +718,13 @@ pa_status pa_sync(pa_ctx* ctx, void* stream) {
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return set_err(ctx, PA_ERR_CUDA, cudaGetErrorString(e));
+  int err = 0;
+  e = cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_err(ctx, PA_ERR_CUDA, cudaGetErrorString(e));
+  if (err) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return set_err(ctx, PA_ERR_TIMEOUT, "a bounded device wait ran out (shared-memory tile load)");
+  }
   return PA_OK;
 }
 

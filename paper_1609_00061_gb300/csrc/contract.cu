@@ -7,6 +7,11 @@
 // row (b, m) of C is the OR of the rows B[b][k][:] selected by the set bits of
 // row (b, m) of A.  Curve plots are sparse, so the work is proportional to the
 // number of set bits of A times the packed width of B, not to M*K*N.
+#include <cuda.h>
+#include <string.h>
+
+#include <algorithm>
+
 #include "pa_internal.h"
 
 namespace pa {
@@ -81,110 +86,240 @@ void launch_reshape(const ReshapeDesc& d, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- row-OR
-// Lanes form groups of G (a power of two <= 32).  A group owns one task
-// (output row, k-chunk, n-chunk); lane l of the group accumulates the words
-// n = n0 + l + G*j, j < NJ, of that row.  The A words of the task are read by
-// the group together and their set bits walked with ffs.
-template <int G, int NJ>
-__global__ void __launch_bounds__(256) rowor_kernel(const RowOrDesc d) {
-  const int lane = threadIdx.x & 31;
-  const int grp = lane / G, lig = lane % G;
-  constexpr int kGroups = 32 / G;
-  const int64_t nrows = d.nbatch * d.M;
-  const int64_t ntasks = nrows * d.nkchunks * d.nnchunks;
-  const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // lanes of one group run in lockstep (same task, same loop bounds), so the
-  // group's own mask suffices for its shuffles
+// One CTA owns the tile B[b][k0 .. k0+Kc)[n0 .. n0+Nt) in shared memory, staged
+// by the Tensor Memory Accelerator (2-D boxes of 256 rows x Nt words) when the
+// row pitch allows it, else by plain loads.  Its warps then walk output rows:
+// lanes form groups of G = Nt, a group owns one output row, reads the row's A
+// words for this K range together, and for every set bit k ORs shared row
+// k - k0 into its accumulator (lane l holds word n0 + l).  Up to four set bits
+// are resolved per round so that their shared-memory loads overlap; a missing
+// bit points at an all-zero sentinel row after the tile.
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after about `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit_ns) {
+  const long long t0 = clock64();
+  const long long limit_cycles = limit_ns * 2;  // >= 1 cycle per ns at <= 2.1 GHz
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit_cycles) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int take_bit(uint64_t& aw, int base, int kc_len) {
+  if (!aw) return kc_len;
+  const int bit = __ffsll((long long)aw) - 1;
+  aw &= aw - 1;
+  const int i = base + bit;
+  return i < kc_len ? i : kc_len;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256)
+rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
+  extern __shared__ __align__(1024) uint64_t bs[];
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  int64_t cta = blockIdx.x;
+  const int64_t rs = cta % d.row_splits;
+  cta /= d.row_splits;
+  const int64_t kc = cta % d.k_chunks;
+  cta /= d.k_chunks;
+  const int64_t nt = cta % d.n_tiles;
+  const int64_t b = cta / d.n_tiles;
+  const int64_t k0 = kc * d.Kc;
+  const int kc_len = (int)min((int64_t)d.Kc, d.K - k0);
+  const int64_t n0 = nt * G;
+
+  // ---- stage the B tile
+  if (d.use_tma) {
+    const int nbox = (kc_len + 255) / 256;
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)nbox * 256u * (uint32_t)G * 8u;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
+                   "r"(bytes)
+                   : "memory");
+      for (int j = 0; j < nbox; ++j) {
+        const int x = (int)n0;
+        const int y = (int)(b * d.K + k0 + 256 * j);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(bs + (size_t)j * 256 * G)),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_u32(&bar))
+            : "memory");
+      }
+    }
+    const bool ok = mbar_wait(&bar, 0, 1000000000ll);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(d.err, 1);
+      return;
+    }
+  } else {
+    for (int idx = tid; idx < kc_len * G; idx += blockDim.x) {
+      const int r = idx / G, c = idx % G;
+      const int64_t n = n0 + c;
+      bs[idx] = (n < d.Nw) ? __ldg(d.B + (b * d.K + k0 + r) * d.Nw + n) : 0ull;
+    }
+  }
+  if (tid < G) bs[(size_t)kc_len * G + tid] = 0ull;  // sentinel row
+  __syncthreads();
+
+  // ---- output rows
+  const int lane = tid & 31, grp = lane / G, lig = lane % G;
+  constexpr int kGroupsPerWarp = 32 / G;
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  for (int64_t t = warp_global * kGroups + grp; t < ntasks; t += nwarps * kGroups) {
-    const int64_t nc = t % d.nnchunks;
-    const int64_t t2 = t / d.nnchunks;
-    const int64_t kc = t2 % d.nkchunks;
-    const int64_t row = t2 / d.nkchunks;
-    const int64_t b = row / d.M;
+  const int64_t m_begin = rs * d.rows_per_split;
+  const int64_t m_end = min(d.M, m_begin + d.rows_per_split);
+  const int64_t kw0 = k0 / 64;
+  const int64_t kw1 = min(d.a_row_words, (k0 + kc_len + 63) / 64);
+  const int64_t n = n0 + lig;
+  for (int64_t m = m_begin + (tid >> 5) * kGroupsPerWarp + grp; m < m_end;
+       m += (blockDim.x >> 5) * kGroupsPerWarp) {
+    const int64_t row = b * d.M + m;
     const uint64_t* __restrict__ arow = d.A + row * d.a_row_words;
-    const uint64_t* __restrict__ bmat = d.B + b * d.K * d.Nw;
-    const int64_t n0 = nc * (int64_t)(G * NJ);
-    uint64_t acc[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) acc[j] = 0;
-    const int64_t kw0 = kc * d.kchunk_words;
-    const int64_t kw1 = min(kw0 + d.kchunk_words, d.a_row_words);
+    uint64_t acc = 0;
     for (int64_t kb = kw0; kb < kw1; kb += G) {
-      // the group loads up to G words of A at once, then walks them in turn
-      const int64_t myk = kb + lig;
-      const uint64_t mw = (myk < kw1) ? __ldg(arow + myk) : 0ull;
+      const uint64_t mw = (kb + lig < kw1) ? __ldg(arow + kb + lig) : 0ull;
       const int cnt = (int)min((int64_t)G, kw1 - kb);
       for (int q = 0; q < cnt; ++q) {
         uint64_t aw = __shfl_sync(gmask, mw, grp * G + q);
+        const int base = (int)((kb + q) * 64 - k0);
         while (aw) {
-          const int bit = __ffsll((long long)aw) - 1;
-          aw &= aw - 1;
-          const int64_t k = (kb + q) * 64 + bit;
-          if (k >= d.K) break;  // padding bits of a caller's array are ignored
-          const uint64_t* __restrict__ brow = bmat + k * d.Nw;
-#pragma unroll
-          for (int j = 0; j < NJ; ++j) {
-            const int64_t n = n0 + lig + (int64_t)G * j;
-            if (n < d.Nw) acc[j] |= __ldg(brow + n);
-          }
+          const int i0 = take_bit(aw, base, kc_len);
+          const int i1 = take_bit(aw, base, kc_len);
+          const int i2 = take_bit(aw, base, kc_len);
+          const int i3 = take_bit(aw, base, kc_len);
+          acc |= bs[(size_t)i0 * G + lig] | bs[(size_t)i1 * G + lig] |
+                 bs[(size_t)i2 * G + lig] | bs[(size_t)i3 * G + lig];
         }
       }
     }
-    uint64_t* crow = d.C + row * d.Nw;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int64_t n = n0 + lig + (int64_t)G * j;
-      if (n < d.Nw) {
-        if (d.atomic) {
-          if (acc[j]) atomicOr((unsigned long long*)(crow + n), (unsigned long long)acc[j]);
-        } else {
-          crow[n] = acc[j];
-        }
+    if (n < d.Nw) {
+      uint64_t* c = d.C + row * d.Nw + n;
+      if (d.atomic) {
+        if (acc) atomicOr((unsigned long long*)c, (unsigned long long)acc);
+      } else {
+        *c = acc;
       }
     }
   }
 }
 
-void launch_rowor(const RowOrDesc& d, cudaStream_t s) {
-  const int64_t nrows = d.nbatch * d.M;
-  if (nrows <= 0 || d.Nw <= 0) return;
-  int G = 1;
-  while (G < 32 && G < d.Nw) G <<= 1;
-  int NJ = 1;
-  if (d.Nw > 32) NJ = (d.Nw >= 256) ? 8 : (d.Nw >= 128 ? 4 : (d.Nw >= 64 ? 2 : 1));
-  const int64_t groups = nrows * d.nkchunks * d.nnchunks;
-  const int64_t warps = (groups + (32 / G) - 1) / (32 / G);
-  int64_t blocks = (warps + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
-  const unsigned gb = (unsigned)blocks;
-#define PA_ROWOR(GG, NN) rowor_kernel<GG, NN><<<gb, 256, 0, s>>>(d)
-  switch (G) {
-    case 1: PA_ROWOR(1, 1); break;
-    case 2: PA_ROWOR(2, 1); break;
-    case 4: PA_ROWOR(4, 1); break;
-    case 8: PA_ROWOR(8, 1); break;
-    case 16: PA_ROWOR(16, 1); break;
-    default:
-      switch (NJ) {
-        case 1: PA_ROWOR(32, 1); break;
-        case 2: PA_ROWOR(32, 2); break;
-        case 4: PA_ROWOR(32, 4); break;
-        default: PA_ROWOR(32, 8); break;
-      }
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+constexpr size_t kTileBudget = 160 * 1024;  // shared bytes for one B tile
+
+}  // namespace
+
+void rowor_plan(RowOrDesc& d) {
+  // widest power-of-two tile (<= 32 words, <= the row) whose K range fits the budget
+  int nt_max = 1;
+  while (nt_max < 32 && nt_max < d.Nw) nt_max <<= 1;
+  int Nt = nt_max;
+  while (Nt > 2 && (size_t)(d.K + 1) * Nt * 8 > kTileBudget) Nt >>= 1;
+  d.Nt = Nt;
+  int64_t kc = (int64_t)(kTileBudget / ((size_t)Nt * 8)) - 1;
+  const bool tma_ok = (d.Nw % 2 == 0) && (Nt % 2 == 0) &&
+                      (reinterpret_cast<uintptr_t>(d.B) % 16 == 0) &&
+                      (d.nbatch * d.K < (1ll << 31)) && encode_fn() != nullptr;
+  d.use_tma = tma_ok ? 1 : 0;
+  if (tma_ok) {
+    // the staged rows are whole 256-row boxes, plus the sentinel row
+    d.Kc = (int32_t)(((d.K + 255) / 256 * 256 <= kc) ? d.K : std::max<int64_t>(256, kc / 256 * 256));
+  } else {
+    d.Kc = (int32_t)((d.K <= kc) ? d.K : std::max<int64_t>(64, kc / 64 * 64));
+  }
+  d.n_tiles = (d.Nw + Nt - 1) / Nt;
+  d.k_chunks = (d.K + d.Kc - 1) / d.Kc;
+  d.atomic = d.k_chunks > 1 ? 1 : 0;
+  const size_t smem = rowor_smem_bytes(d);
+  const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(8, (227 * 1024) / (smem + 1024)));
+  const int64_t base = d.nbatch * d.n_tiles * d.k_chunks;
+  const int64_t target = 152 * per_sm;
+  int64_t splits = (target + base - 1) / base;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, (d.M + 7) / 8));
+  d.rows_per_split = (d.M + splits - 1) / splits;
+  d.row_splits = (d.M + d.rows_per_split - 1) / d.rows_per_split;
+}
+
+size_t rowor_smem_bytes(const RowOrDesc& d) {
+  const int64_t rows = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
+  return (size_t)(rows + 1) * d.Nt * 8;
+}
+
+cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s) {
+  const int64_t grid = d.nbatch * d.n_tiles * d.k_chunks * d.row_splits;
+  if (grid <= 0) return cudaSuccess;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof tmap);
+  if (d.use_tma) {
+    const cuuint64_t dims[2] = {(cuuint64_t)d.Nw, (cuuint64_t)(d.nbatch * d.K)};
+    const cuuint64_t strides[1] = {(cuuint64_t)d.Nw * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)d.Nt, 256u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+                             const_cast<uint64_t*>(d.B), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  const size_t smem = rowor_smem_bytes(d);
+#define PA_ROWOR(GG)                                                                         \
+  do {                                                                                       \
+    cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                         (int)smem);                                                         \
+    rowor_tile_kernel<GG><<<(unsigned)grid, 256, smem, s>>>(tmap, d);                        \
+  } while (0)
+  switch (d.Nt) {
+    case 1: PA_ROWOR(1); break;
+    case 2: PA_ROWOR(2); break;
+    case 4: PA_ROWOR(4); break;
+    case 8: PA_ROWOR(8); break;
+    case 16: PA_ROWOR(16); break;
+    default: PA_ROWOR(32); break;
   }
 #undef PA_ROWOR
-}
-
-// Number of words of one output row handled by one task for this shape.
-int64_t rowor_chunk_words(int64_t Nw) {
-  int G = 1;
-  while (G < 32 && G < Nw) G <<= 1;
-  int NJ = 1;
-  if (Nw > 32) NJ = (Nw >= 256) ? 8 : (Nw >= 128 ? 4 : (Nw >= 64 ? 2 : 1));
-  return (int64_t)G * NJ;
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- AND

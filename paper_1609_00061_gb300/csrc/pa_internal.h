@@ -48,8 +48,10 @@ struct AxisTableJob {
 
 void launch_axis_tables(const AxisTableJob* d_jobs, int njobs, int64_t total, double* x64,
                         float* x32, cudaStream_t s);
+// common_degree: the degree shared by every job (selects a specialised kernel),
+// or -1 when they differ
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
-                 int max_degree, cudaStream_t s);
+                 int max_degree, int common_degree, cudaStream_t s);
 
 // ------------------------------------------------------------- bit arrays
 // A bit-packed array with `inner` trailing axes flattened into packed rows:
@@ -98,19 +100,25 @@ struct ReshapeDesc {
 void launch_reshape(const ReshapeDesc& d, cudaStream_t s);
 
 // C[b*M + m, :] |= B[b*K + k, :] for every set bit k of A[b*M + m, :].
+// One CTA owns a tile of B (Kc rows x Nt words of batch b) in shared memory and
+// a run of output rows; see contract.cu.
 struct RowOrDesc {
   const uint64_t* A;
   const uint64_t* B;
   uint64_t* C;
   int64_t nbatch, M, K, Nw;   // Nw = words per B / C row
   int64_t a_row_words;        // = ceil(K / 64)
-  int64_t kchunk_words;       // A words per task
-  int64_t nkchunks, nnchunks;
+  int32_t Nt;                 // words per tile (power of two <= 32)
+  int32_t Kc;                 // B rows per tile (multiple of 256 when use_tma)
+  int64_t n_tiles, k_chunks, row_splits, rows_per_split;
   int32_t atomic;             // 1: C pre-zeroed, results OR-ed in atomically
+  int32_t use_tma;            // 1: stage the tile with cp.async.bulk.tensor
+  int* err;                   // device error word: set when a bounded wait runs out
 };
-void launch_rowor(const RowOrDesc& d, cudaStream_t s);
-// words of one output row that one row-OR task covers (its n-chunk width)
-int64_t rowor_chunk_words(int64_t Nw);
+// Choose the tile shape and grid for a contraction of this shape.
+void rowor_plan(RowOrDesc& d);
+size_t rowor_smem_bytes(const RowOrDesc& d);
+cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s);
 // cudaSuccess when this build holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
