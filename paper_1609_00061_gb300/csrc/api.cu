@@ -453,7 +453,7 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
   std::vector<char> blob;
   std::vector<size_t> coeff_off(nrel);
   int64_t tiles = 0;
-  int max_rows = 1, max_deg = 0, common_deg = rels[0].degree;
+  int max_rows = 1, max_deg = 0, common_deg = rels[0].degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = rels[i];
     std::vector<int> dv = distinct_vars(r);
@@ -486,10 +486,22 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
       J.x64[p] = x64 + toff[r.vars[p]];
     }
     J.x32_last = x32 + toff[r.vars[r.arity - 1]];
+    {
+      const pa_axis& ax = axes[r.vars[r.arity - 1]];
+      J.ymax = (float)(fmax(fabs(ax.lo), fabs(ax.hi)) * (1.0 + 0x1p-20));
+      // coefficients with e_last = j form block j of the nest order; its size is
+      // the number of monomials of arity-1 variables of degree <= D - j
+      int32_t off = 0;
+      for (int j = 0; j <= r.degree; ++j) {
+        J.block_off[j] = off;
+        off += (int32_t)coeff_count(r.arity - 1, r.degree - j);
+      }
+    }
     J.hoisted = (a.ndim == r.arity) ? 1 : 0;
     J.nrows = a.nrows();
     J.row_words = a.row_words();
     J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, 512 / J.row_words));
+    max_res_last = std::max(max_res_last, (int)a.res[a.ndim - 1]);
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
@@ -531,7 +543,7 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
   ex.before("plot_kernel");
   if (!ex.dry) {
     launch_plot(reinterpret_cast<const PlotJob*>(dblob + jobs_off), nrel, tiles, max_rows,
-                max_deg, common_deg, ex.s);
+                max_deg, common_deg, max_res_last, ex.s);
   }
   ex.launched("plot_kernel");
   return plots;

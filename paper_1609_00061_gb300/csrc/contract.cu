@@ -88,13 +88,20 @@ void launch_reshape(const ReshapeDesc& d, cudaStream_t s) {
 // ---------------------------------------------------------------- row-OR
 // One CTA owns the tile B[b][k0 .. k0+Kc)[n0 .. n0+Nt) in shared memory, staged
 // by the Tensor Memory Accelerator (2-D boxes of 256 rows x Nt words) when the
-// row pitch allows it, else by plain loads.  Its warps then walk output rows:
-// lanes form groups of G = Nt, a group owns one output row, reads the row's A
-// words for this K range together, and for every set bit k ORs shared row
-// k - k0 into its accumulator (lane l holds word n0 + l).  Up to four set bits
-// are resolved per round so that their shared-memory loads overlap; a missing
-// bit points at an all-zero sentinel row after the tile.
+// row pitch allows it, else by plain loads, followed by an all-zero sentinel
+// row.  Each warp then takes one output row at a time:
+//   1. its lanes load up to 32 words of the row's A bits for this K range,
+//      count their set bits and prefix-sum the counts across the warp;
+//   2. every lane writes the tile-row indices of its set bits into the warp's
+//      list in shared memory (bits past the tile point at the sentinel);
+//   3. the warp splits into 32/Nt groups of Nt lanes; group g ORs tile rows
+//      list[g], list[g + 32/Nt], ... (four loads in flight per lane), lane l of
+//      a group holding word n0 + l;
+//   4. the groups' words are OR-ed together with shuffles and stored.
 namespace {
+
+constexpr int kRowOrThreads = 512;
+constexpr int kListCap = 32 * 64;  // one batch of 32 A words
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -118,20 +125,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return false;
 }
 
-__device__ __forceinline__ int take_bit(uint64_t& aw, int base, int kc_len) {
-  if (!aw) return kc_len;
-  const int bit = __ffsll((long long)aw) - 1;
-  aw &= aw - 1;
-  const int i = base + bit;
-  return i < kc_len ? i : kc_len;
-}
-
 template <int G>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kRowOrThreads)
 rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
   extern __shared__ __align__(1024) uint64_t bs[];
-  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
+  const int nwarps = blockDim.x >> 5;
+  const int64_t staged = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
+  uint16_t* lists = reinterpret_cast<uint16_t*>(bs + (staged + 1) * G);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(lists + (size_t)nwarps * kListCap);
+
   int64_t cta = blockIdx.x;
   const int64_t rs = cta % d.row_splits;
   cta /= d.row_splits;
@@ -147,14 +150,14 @@ rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
   if (d.use_tma) {
     const int nbox = (kc_len + 255) / 256;
     if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)nbox * 256u * (uint32_t)G * 8u;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                    "r"(bytes)
                    : "memory");
       for (int j = 0; j < nbox; ++j) {
@@ -163,11 +166,11 @@ rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(bs + (size_t)j * 256 * G)),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_u32(&bar))
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
             : "memory");
       }
     }
-    const bool ok = mbar_wait(&bar, 0, 1000000000ll);
+    const bool ok = mbar_wait(bar, 0, 1000000000ll);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(d.err, 1);
       return;
@@ -182,37 +185,53 @@ rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
   if (tid < G) bs[(size_t)kc_len * G + tid] = 0ull;  // sentinel row
   __syncthreads();
 
-  // ---- output rows
-  const int lane = tid & 31, grp = lane / G, lig = lane % G;
-  constexpr int kGroupsPerWarp = 32 / G;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  // ---- output rows, one warp each
+  const int warp = tid >> 5, lane = tid & 31;
+  const int grp = lane / G, lig = lane % G;
+  constexpr int P = 32 / G;
+  uint16_t* list = lists + (size_t)warp * kListCap;
   const int64_t m_begin = rs * d.rows_per_split;
   const int64_t m_end = min(d.M, m_begin + d.rows_per_split);
   const int64_t kw0 = k0 / 64;
   const int64_t kw1 = min(d.a_row_words, (k0 + kc_len + 63) / 64);
-  const int64_t n = n0 + lig;
-  for (int64_t m = m_begin + (tid >> 5) * kGroupsPerWarp + grp; m < m_end;
-       m += (blockDim.x >> 5) * kGroupsPerWarp) {
+  for (int64_t m = m_begin + warp; m < m_end; m += nwarps) {
     const int64_t row = b * d.M + m;
     const uint64_t* __restrict__ arow = d.A + row * d.a_row_words;
     uint64_t acc = 0;
-    for (int64_t kb = kw0; kb < kw1; kb += G) {
-      const uint64_t mw = (kb + lig < kw1) ? __ldg(arow + kb + lig) : 0ull;
-      const int cnt = (int)min((int64_t)G, kw1 - kb);
-      for (int q = 0; q < cnt; ++q) {
-        uint64_t aw = __shfl_sync(gmask, mw, grp * G + q);
-        const int base = (int)((kb + q) * 64 - k0);
-        while (aw) {
-          const int i0 = take_bit(aw, base, kc_len);
-          const int i1 = take_bit(aw, base, kc_len);
-          const int i2 = take_bit(aw, base, kc_len);
-          const int i3 = take_bit(aw, base, kc_len);
-          acc |= bs[(size_t)i0 * G + lig] | bs[(size_t)i1 * G + lig] |
-                 bs[(size_t)i2 * G + lig] | bs[(size_t)i3 * G + lig];
-        }
+    for (int64_t wb = kw0; wb < kw1; wb += 32) {
+      const int64_t kwl = wb + lane;
+      uint64_t a = (kwl < kw1) ? __ldg(arow + kwl) : 0ull;
+      const int c = __popcll(a);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
       }
+      const int T = __shfl_sync(0xffffffffu, incl, 31);
+      int off = incl - c;
+      const int base = (int)(kwl * 64 - k0);
+      while (a) {
+        const int bit = __ffsll((long long)a) - 1;
+        a &= a - 1;
+        const int i = base + bit;
+        list[off++] = (uint16_t)(i < kc_len ? i : kc_len);
+      }
+      __syncwarp();
+      for (int e = grp; e < T; e += 4 * P) {
+        const int i0 = list[e];
+        const int i1 = (e + P < T) ? list[e + P] : kc_len;
+        const int i2 = (e + 2 * P < T) ? list[e + 2 * P] : kc_len;
+        const int i3 = (e + 3 * P < T) ? list[e + 3 * P] : kc_len;
+        acc |= bs[(size_t)i0 * G + lig] | bs[(size_t)i1 * G + lig] | bs[(size_t)i2 * G + lig] |
+               bs[(size_t)i3 * G + lig];
+      }
+      __syncwarp();
     }
-    if (n < d.Nw) {
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    const int64_t n = n0 + lane;
+    if (lane < G && n < d.Nw) {
       uint64_t* c = d.C + row * d.Nw + n;
       if (d.atomic) {
         if (acc) atomicOr((unsigned long long*)c, (unsigned long long)acc);
@@ -245,7 +264,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-constexpr size_t kTileBudget = 160 * 1024;  // shared bytes for one B tile
+constexpr size_t kTileBudget = 160 * 1024;  // shared bytes for one B tile (lists: 64 KB more)
 
 }  // namespace
 
@@ -275,14 +294,14 @@ void rowor_plan(RowOrDesc& d) {
   const int64_t base = d.nbatch * d.n_tiles * d.k_chunks;
   const int64_t target = 152 * per_sm;
   int64_t splits = (target + base - 1) / base;
-  splits = std::max<int64_t>(1, std::min<int64_t>(splits, (d.M + 7) / 8));
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, (d.M + 15) / 16));
   d.rows_per_split = (d.M + splits - 1) / splits;
   d.row_splits = (d.M + d.rows_per_split - 1) / d.rows_per_split;
 }
 
 size_t rowor_smem_bytes(const RowOrDesc& d) {
   const int64_t rows = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
-  return (size_t)(rows + 1) * d.Nt * 8;
+  return (size_t)(rows + 1) * d.Nt * 8 + (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16;
 }
 
 cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s) {
@@ -308,7 +327,7 @@ cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s) {
   do {                                                                                       \
     cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          (int)smem);                                                         \
-    rowor_tile_kernel<GG><<<(unsigned)grid, 256, smem, s>>>(tmap, d);                        \
+    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(tmap, d);                        \
   } while (0)
   switch (d.Nt) {
     case 1: PA_ROWOR(1); break;

@@ -37,6 +37,8 @@ struct PlotJob {
   float eps32;                      // eps rounded to FP32
   float kfac;                       // FP32 filter: error bound factor on sum |g_j y^j|
   float abs_margin;                 // FP32 filter: margin for eps rounding / underflow
+  float ymax;                       // >= |y| for every FP32 centre of the last port
+  int32_t block_off[kMaxDeg + 1];   // nest-order offset of the coefficients with e_last = j
 };
 
 // Centre tables: x64[off_v + i] = lo_v + ((double)i + 0.5) * ((hi_v - lo_v) / res_v).
@@ -51,7 +53,7 @@ void launch_axis_tables(const AxisTableJob* d_jobs, int njobs, int64_t total, do
 // common_degree: the degree shared by every job (selects a specialised kernel),
 // or -1 when they differ
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
-                 int max_degree, int common_degree, cudaStream_t s);
+                 int max_degree, int common_degree, int max_res_last, cudaStream_t s);
 
 // ------------------------------------------------------------- bit arrays
 // A bit-packed array with `inner` trailing axes flattened into packed rows:

@@ -75,29 +75,22 @@ __device__ __forceinline__ bool decide64(double f, int kind, double eps, int str
 }
 
 // --------------------------------------------------------------- plot kernel
+// One block plots a tile of rows (all axes but the last fixed):
+//   A1. thread (r, j) computes the row polynomial's coefficient g_j in FP64
+//       (the inner nested sums, exactly as pa.h orders them) and its FP32 copy;
+//       the FP32 centres of the last axis are copied to shared memory;
+//   A2. thread r bounds the FP32 evaluation error of its row,
+//       B_r = (4D+8) u 1.01 a_r + 2^-21 eps + 1e-30, a_r = sum_j |g_j| Y^j with
+//       Y >= every |y| of the axis, and stores the thresholds eps -+ B_r;
+//   B.  thread per output word: the 64 pixels of the word are evaluated in FP32
+//       (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below eps - B_r is
+//       on, above eps + B_r is off, anything else is decided by the exact FP64
+//       evaluation.  Bits are set directly in the thread's word, so no warp
+//       vote is needed and the row's words are stored coalesced.
 constexpr int kPlotThreads = 256;
+constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
 
-// FP32 filter for one pixel of a hoisted row: 1 = on, 0 = off, 2 = undecided
-// (the FP64 evaluation decides).  DS is the degree when known at compile time.
-template <int DS>
-__device__ __forceinline__ int filter32(float y, const float* g, const float* ga, int D, int kind,
-                                        float eps32, float kfac, float amarg) {
-  const int deg = DS >= 0 ? DS : D;
-  float s = g[0], a = ga[0], pw = 1.0f;
-#pragma unroll
-  for (int j = 1; j <= (DS >= 0 ? DS : kMaxDeg); ++j) {
-    if (DS < 0 && j > deg) break;
-    pw = __fmul_rn(pw, y);
-    s = __fmaf_rn(g[j], pw, s);
-    a = __fmaf_rn(ga[j], fabsf(pw), a);
-  }
-  const float d = (kind == PA_EQ) ? fabsf(s) : s;
-  const float B = __fmaf_rn(a, kfac, amarg);
-  if (!(a <= FLT_MAX)) return 2;
-  if (d > __fadd_rn(eps32, B)) return 0;
-  if (d < __fsub_rn(eps32, B)) return 1;
-  return 2;
-}
+__device__ __forceinline__ int ypad(int i) { return i + (i >> 6); }
 
 // exact FP64 value of sum_j g_j y^j in the order fixed by pa.h
 __device__ __noinline__ bool exact64(double y64, const double* g6, int D, int kind, double eps,
@@ -126,10 +119,8 @@ __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i)
   return decide64(nest_dev(J->arity - 1, J->degree, cp, x), J->kind, J->eps, J->strict);
 }
 
-// phase A: one thread per row computes the row's polynomial in the last port,
-// g_j = the inner nested sums (FP64, the order of pa.h), and its FP32 copies
-__device__ __noinline__ void row_polynomial(const PlotJob* J, int64_t row, int D, double* g64,
-                                            float* g32, float* ga32) {
+// g_j of one row: the nested sums over the first arity-1 ports with e_last = j
+__device__ __noinline__ double row_coeff(const PlotJob* J, int64_t row, int j) {
   const int ndim = J->ndim;
   int64_t rest = row;
   int idx[kMaxDim];
@@ -139,19 +130,13 @@ __device__ __noinline__ void row_polynomial(const PlotJob* J, int64_t row, int D
   }
   double x[kMaxDim];
   for (int p = 0; p < J->arity - 1; ++p) x[p] = J->x64[p][idx[J->port_axis[p]]];
-  const double* cp = J->coeffs;
-  for (int j = 0; j <= D; ++j) {
-    const double g = nest_dev(J->arity - 2, D - j, cp, x);
-    g64[j] = g;
-    const float g1 = __double2float_rn(g);
-    g32[j] = g1;
-    ga32[j] = fabsf(g1);
-  }
+  const double* cp = J->coeffs + J->block_off[j];
+  return nest_dev(J->arity - 2, J->degree - j, cp, x);
 }
 
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
-plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int smem_stride) {
+plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int gstride, int rows_cap, int ytab_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_job;
   if (threadIdx.x == 0) {
@@ -167,7 +152,7 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int smem_stride) {
   const int D = DS >= 0 ? DS : J->degree;
   const int D1 = D + 1;
   const int arity = J->arity;
-  const int64_t row_words = J->row_words;
+  const int row_words = (int)J->row_words;
   const int res_last = J->res[J->ndim - 1];
   const int R = J->rows_per_tile;
   const int64_t row0 = ((int64_t)blockIdx.x - J->tile0) * R;
@@ -177,63 +162,89 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int smem_stride) {
   const bool hoisted = J->hoisted != 0;
 
   double* g64 = reinterpret_cast<double*>(smem);
-  float* g32 = reinterpret_cast<float*>(g64 + smem_stride);
-  float* ga32 = g32 + smem_stride;
+  float* g32 = reinterpret_cast<float*>(g64 + gstride);
+  float* thr = g32 + gstride;                 // [R][2]: eps - B_r, eps + B_r
+  float* ytab = thr + 2 * rows_cap;
+  const bool ysmem = res_last <= ytab_cap;
+  const float* __restrict__ y32g = J->x32_last;
 
   if (hoisted) {
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) row_polynomial(J, row0 + r, D, g64 + r * D1, g32 + r * D1, ga32 + r * D1);
+    for (int t = threadIdx.x; t < nr * D1; t += blockDim.x) {
+      const int r = t / D1, j = t % D1;
+      const double g = row_coeff(J, row0 + r, j);
+      g64[r * D1 + j] = g;
+      g32[r * D1 + j] = __double2float_rn(g);
+    }
+    if (ysmem)
+      for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = y32g[i];
+    __syncthreads();
+    const float Y = J->ymax, kfac = J->kfac, amarg = J->abs_margin, eps32 = J->eps32;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      float a = 0.0f, pw = 1.0f;
+      for (int j = 0; j <= D; ++j) {
+        a = __fmaf_rn(fabsf(g32[r * D1 + j]), pw, a);
+        pw = __fmul_rn(pw, Y);
+      }
+      const float B = __fmaf_rn(a, kfac, amarg);
+      float lo = __fsub_rn(eps32, B), hi = __fadd_rn(eps32, B);
+      if (!(a <= FLT_MAX) || !(B <= FLT_MAX)) {
+        lo = -INFINITY;   // nothing is certain: every pixel of the row takes the FP64 path
+        hi = INFINITY;
+      }
+      thr[2 * r] = lo;
+      thr[2 * r + 1] = hi;
+    }
     __syncthreads();
   }
 
-  // phase B: a warp task is (row, run of up to 32 words); lane l evaluates the
-  // pixels 64w + l and 64w + 32 + l of every word w of the run
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int64_t runs_per_row = (row_words + 31) / 32;
-  const int64_t ntasks = (int64_t)nr * runs_per_row;
-  const float* __restrict__ y32t = J->x32_last;
   const double* __restrict__ y64t = J->x64[arity - 1];
-  const float eps32 = J->eps32, kfac = J->kfac, amarg = J->abs_margin;
   uint64_t* __restrict__ out = J->out;
   constexpr int kG = DS >= 0 ? DS + 1 : kMaxDeg + 1;
-  float g[kG], ga[kG];
-
-  for (int64_t t = warp; t < ntasks; t += nwarps) {
-    const int r = (int)(t / runs_per_row);
-    const int64_t w0 = (t % runs_per_row) * 32;
-    const int nw = (int)min((int64_t)32, row_words - w0);
+  const int nwords = nr * row_words;
+  for (int f = threadIdx.x; f < nwords; f += blockDim.x) {
+    const int r = f / row_words, w = f - r * row_words;
+    const int i0 = w * 64;
+    const int nb = min(64, res_last - i0);
+    uint64_t word = 0;
     if (hoisted) {
+      float g[kG];
 #pragma unroll
-      for (int j = 0; j < kG; ++j) {
-        if (DS < 0 && j > D) break;
-        g[j] = g32[r * D1 + j];
-        ga[j] = ga32[r * D1 + j];
+      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? g32[r * D1 + j] : 0.0f;
+      const float lo = thr[2 * r], hi = thr[2 * r + 1];
+      uint64_t pending = 0;
+#pragma unroll 16
+      for (int bb = 0; bb < 64; ++bb) {
+        if (bb < nb) {
+          const int i = i0 + bb;
+          const float y = ysmem ? ytab[ypad(i)] : __ldg(y32g + i);
+          float s = g[0], pw = y;
+          if (DS >= 0) {
+#pragma unroll
+            for (int j = 1; j < kG; ++j) {
+              if (j > 1) pw = __fmul_rn(pw, y);
+              s = __fmaf_rn(g[j], pw, s);
+            }
+          } else {
+            for (int j = 1; j <= D; ++j) {
+              if (j > 1) pw = __fmul_rn(pw, y);
+              s = __fmaf_rn(g[j], pw, s);
+            }
+          }
+          const float dd = (kind == PA_EQ) ? fabsf(s) : s;
+          if (dd < lo) word |= (1ull << bb);
+          else if (!(dd > hi)) pending |= (1ull << bb);
+        }
       }
-    }
-    uint64_t mine = 0;
-    for (int it = 0; it < nw; ++it) {
-      const int64_t i0 = (w0 + it) * 64 + lane;
-      const int64_t i1 = i0 + 32;
-      bool b0 = false, b1 = false;
-      if (hoisted) {
-        const float y0 = (i0 < res_last) ? y32t[i0] : 0.0f;
-        const float y1 = (i1 < res_last) ? y32t[i1] : 0.0f;
-        int c0 = filter32<DS>(y0, g, ga, D, kind, eps32, kfac, amarg);
-        int c1 = filter32<DS>(y1, g, ga, D, kind, eps32, kfac, amarg);
-        if (i0 >= res_last) c0 = 0;
-        if (i1 >= res_last) c1 = 0;
-        if (c0 == 2) c0 = exact64(y64t[i0], g64 + r * D1, D, kind, eps, strict);
-        if (c1 == 2) c1 = exact64(y64t[i1], g64 + r * D1, D, kind, eps, strict);
-        b0 = c0 != 0;
-        b1 = c1 != 0;
-      } else {
-        if (i0 < res_last) b0 = general64(J, row0 + r, i0);
-        if (i1 < res_last) b1 = general64(J, row0 + r, i1);
+      while (pending) {
+        const int bb = __ffsll((long long)pending) - 1;
+        pending &= pending - 1;
+        if (exact64(y64t[i0 + bb], g64 + r * D1, D, kind, eps, strict)) word |= (1ull << bb);
       }
-      const unsigned lo = __ballot_sync(0xffffffffu, b0);
-      const unsigned hi = __ballot_sync(0xffffffffu, b1);
-      if (lane == it) mine = ((uint64_t)hi << 32) | lo;
+    } else {
+      for (int bb = 0; bb < nb; ++bb)
+        if (general64(J, row0 + r, i0 + bb)) word |= (1ull << bb);
     }
-    if (lane < nw) out[(row0 + r) * row_words + w0 + lane] = mine;
+    out[(row0 + r) * (int64_t)row_words + w] = word;
   }
 }
 
@@ -243,18 +254,27 @@ cudaError_t probe_kernel_image() {
 }
 
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
-                 int max_degree, int common_degree, cudaStream_t s) {
+                 int max_degree, int common_degree, int max_res_last, cudaStream_t s) {
   if (total_tiles <= 0) return;
-  const int stride = max_rows_per_tile * (max_degree + 1);
-  const size_t smem = (size_t)stride * (sizeof(double) + 2 * sizeof(float));
+  const int gstride = max_rows_per_tile * (max_degree + 1);
+  const int ycap = max_res_last <= kYTabCap ? max_res_last : 0;
+  const size_t smem = (size_t)gstride * (sizeof(double) + sizeof(float)) +
+                      (size_t)max_rows_per_tile * 2 * sizeof(float) +
+                      (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
   const unsigned grid = (unsigned)total_tiles;
+#define PA_PLOT(DD)                                                                           \
+  do {                                                                                        \
+    cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, gstride, max_rows_per_tile, ycap);           \
+  } while (0)
   switch (common_degree) {
-    case 1: plot_kernel<1><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, stride); break;
-    case 2: plot_kernel<2><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, stride); break;
-    case 3: plot_kernel<3><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, stride); break;
-    case 4: plot_kernel<4><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, stride); break;
-    default: plot_kernel<-1><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, stride); break;
+    case 1: PA_PLOT(1); break;
+    case 2: PA_PLOT(2); break;
+    case 3: PA_PLOT(3); break;
+    case 4: PA_PLOT(4); break;
+    default: PA_PLOT(-1); break;
   }
+#undef PA_PLOT
 }
 
 }  // namespace pa
