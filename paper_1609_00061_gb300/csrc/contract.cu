@@ -190,11 +190,13 @@ rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
   const int grp = lane / G, lig = lane % G;
   constexpr int P = 32 / G;
   uint16_t* list = lists + (size_t)warp * kListCap;
-  const int64_t m_begin = rs * d.rows_per_split;
-  const int64_t m_end = min(d.M, m_begin + d.rows_per_split);
+  // rows are dealt out cyclically over every warp of the CTAs sharing this
+  // tile, so that runs of dense rows (curves are locally thick) are spread out
+  const int64_t gw = rs * nwarps + warp;
+  const int64_t gstride = d.row_splits * nwarps;
   const int64_t kw0 = k0 / 64;
   const int64_t kw1 = min(d.a_row_words, (k0 + kc_len + 63) / 64);
-  for (int64_t m = m_begin + warp; m < m_end; m += nwarps) {
+  for (int64_t m = gw; m < d.M; m += gstride) {
     const int64_t row = b * d.M + m;
     const uint64_t* __restrict__ arow = d.A + row * d.a_row_words;
     uint64_t acc = 0;

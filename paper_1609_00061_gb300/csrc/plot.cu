@@ -134,6 +134,46 @@ __device__ __noinline__ double row_coeff(const PlotJob* J, int64_t row, int j) {
   return nest_dev(J->arity - 2, J->degree - j, cp, x);
 }
 
+// The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
+// certainly on, bit b of *pending when only the FP64 evaluation can decide.
+template <int DS, bool EQ, bool YS>
+__device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
+                                          const float* ytab_w, const float* __restrict__ y32_w,
+                                          int nb, uint64_t* on, uint64_t* pending) {
+  uint32_t on_lo = 0, on_hi = 0, pe_lo = 0, pe_hi = 0;
+#pragma unroll
+  for (int bb = 0; bb < 64; ++bb) {
+    if (bb < nb) {
+      const float y = YS ? ytab_w[bb] : __ldg(y32_w + bb);
+      float s = g[0], pw = y;
+      if (DS >= 0) {
+#pragma unroll
+        for (int j = 1; j <= (DS >= 0 ? DS : 1); ++j) {
+          if (j > 1) pw = __fmul_rn(pw, y);
+          s = __fmaf_rn(g[j], pw, s);
+        }
+      } else {
+        for (int j = 1; j <= D; ++j) {
+          if (j > 1) pw = __fmul_rn(pw, y);
+          s = __fmaf_rn(g[j], pw, s);
+        }
+      }
+      const float dd = EQ ? fabsf(s) : s;
+      const bool c_on = dd < lo;
+      const bool c_pe = !c_on && !(dd > hi);
+      if (bb < 32) {
+        if (c_on) on_lo |= 1u << bb;
+        if (c_pe) pe_lo |= 1u << bb;
+      } else {
+        if (c_on) on_hi |= 1u << (bb - 32);
+        if (c_pe) pe_hi |= 1u << (bb - 32);
+      }
+    }
+  }
+  *on = ((uint64_t)on_hi << 32) | on_lo;
+  *pending = ((uint64_t)pe_hi << 32) | pe_lo;
+}
+
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
 plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int gstride, int rows_cap, int ytab_cap) {
@@ -212,28 +252,14 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int gstride, int rows_c
       for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? g32[r * D1 + j] : 0.0f;
       const float lo = thr[2 * r], hi = thr[2 * r + 1];
       uint64_t pending = 0;
-#pragma unroll 16
-      for (int bb = 0; bb < 64; ++bb) {
-        if (bb < nb) {
-          const int i = i0 + bb;
-          const float y = ysmem ? ytab[ypad(i)] : __ldg(y32g + i);
-          float s = g[0], pw = y;
-          if (DS >= 0) {
-#pragma unroll
-            for (int j = 1; j < kG; ++j) {
-              if (j > 1) pw = __fmul_rn(pw, y);
-              s = __fmaf_rn(g[j], pw, s);
-            }
-          } else {
-            for (int j = 1; j <= D; ++j) {
-              if (j > 1) pw = __fmul_rn(pw, y);
-              s = __fmaf_rn(g[j], pw, s);
-            }
-          }
-          const float dd = (kind == PA_EQ) ? fabsf(s) : s;
-          if (dd < lo) word |= (1ull << bb);
-          else if (!(dd > hi)) pending |= (1ull << bb);
-        }
+      const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
+      const float* y32_w = y32g + i0;
+      if (kind == PA_EQ) {
+        if (ysmem) eval_word<DS, true, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        else eval_word<DS, true, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+      } else {
+        if (ysmem) eval_word<DS, false, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        else eval_word<DS, false, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
       }
       while (pending) {
         const int bb = __ffsll((long long)pending) - 1;
