@@ -425,34 +425,16 @@ void check_array(pa_ctx* ctx, const pa_array* a, const char* name) {
 
 // ------------------------------------------------------------ plotting
 // Plot all relations into fresh workspace arrays (or into `direct_out`, when
-// given, for a single relation).
+// given, for a single relation): one preparation launch (row polynomials,
+// thresholds, FP32 centre tables) and one plot launch for all of them.
 std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32_t nrel,
                              const pa_relation* rels, int strict, const BitArr* direct_out) {
-  // centre tables for every variable in use
-  std::vector<int64_t> toff(nvars, -1);
-  std::vector<AxisTableJob> tjobs;
-  int64_t ttotal = 0;
-  for (int i = 0; i < nrel; ++i)
-    for (int p = 0; p < rels[i].arity; ++p) {
-      const int v = rels[i].vars[p];
-      if (toff[v] >= 0) continue;
-      toff[v] = ttotal;
-      AxisTableJob j;
-      j.lo = axes[v].lo;
-      j.hi = axes[v].hi;
-      j.res = axes[v].res;
-      j.off = ttotal;
-      tjobs.push_back(j);
-      ttotal += axes[v].res;
-    }
-  double* x64 = static_cast<double*>(ex.alloc((size_t)ttotal * 8));
-  float* x32 = static_cast<float*>(ex.alloc((size_t)ttotal * 4));
-
+  (void)nvars;
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<char> blob;
   std::vector<size_t> coeff_off(nrel);
-  int64_t tiles = 0;
+  int64_t tiles = 0, prep_items = 0;
   int max_rows = 1, max_deg = 0, common_deg = rels[0].degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = rels[i];
@@ -482,10 +464,24 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
     J.ndim = a.ndim;
     for (int k = 0; k < a.ndim; ++k) J.res[k] = (int32_t)a.res[k];
     for (int p = 0; p < r.arity; ++p) {
+      const pa_axis& ax = axes[r.vars[p]];
       J.port_axis[p] = axis_of(a, r.vars[p]);
-      J.x64[p] = x64 + toff[r.vars[p]];
+      J.lo[p] = ax.lo;
+      J.delta[p] = (ax.hi - ax.lo) / (double)ax.res;
     }
-    J.x32_last = x32 + toff[r.vars[r.arity - 1]];
+    J.hoisted = (a.ndim == r.arity) ? 1 : 0;
+    J.nrows = a.nrows();
+    J.row_words = a.row_words();
+    const int64_t res_last = a.res[a.ndim - 1];
+    const int D1 = r.degree + 1;
+    if (J.hoisted) {
+      J.g64 = static_cast<double*>(ex.alloc((size_t)J.nrows * D1 * 8));
+      J.g32 = static_cast<float*>(ex.alloc((size_t)J.nrows * D1 * 4));
+      J.thr = static_cast<float*>(ex.alloc((size_t)J.nrows * 2 * 4));
+      J.y32 = static_cast<float*>(ex.alloc((size_t)res_last * 4));
+      J.prep0 = prep_items;
+      prep_items += J.nrows + res_last;
+    }
     {
       const pa_axis& ax = axes[r.vars[r.arity - 1]];
       J.ymax = (float)(fmax(fabs(ax.lo), fabs(ax.hi)) * (1.0 + 0x1p-20));
@@ -497,15 +493,12 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
         off += (int32_t)coeff_count(r.arity - 1, r.degree - j);
       }
     }
-    J.hoisted = (a.ndim == r.arity) ? 1 : 0;
-    J.nrows = a.nrows();
-    J.row_words = a.row_words();
     J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, 512 / J.row_words));
-    max_res_last = std::max(max_res_last, (int)a.res[a.ndim - 1]);
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
     max_deg = std::max(max_deg, r.degree);
+    max_res_last = std::max(max_res_last, (int)res_last);
     if (r.degree != common_deg) common_deg = -1;
     const double eps = relation_eps(r, axes);
     J.eps = eps;
@@ -520,11 +513,16 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
     ex.st.pixels_plotted += (double)a.bits();
     ex.st.n_plots++;
   }
+  // prep items are assigned to jobs by binary search on prep0: give the jobs
+  // without preparation work the offset of the next one so the search skips them
+  for (int i = nrel - 1; i >= 0; --i)
+    if (!jobs[i].hoisted) jobs[i].prep0 = (i + 1 < nrel) ? jobs[i + 1].prep0 : prep_items;
   if (tiles > 0x7fffffffLL) throw Fail{set_err(ex.ctx, PA_ERR_TOO_LARGE, "plot grid too large")};
   const size_t jobs_off = blob_put(blob, jobs.data(), jobs.size());
-  const size_t tj_off = blob_put(blob, tjobs.data(), tjobs.size());
-  char* dblob = static_cast<char*>(ex.dry ? ex.alloc(blob.size()) : nullptr);
-  if (!ex.dry) {
+  char* dblob = nullptr;
+  if (ex.dry) {
+    dblob = static_cast<char*>(ex.alloc(blob.size()));
+  } else {
     // patch device coefficient pointers, then upload
     // (the device address of the blob is known only after allocation)
     const size_t off = (ex.used + kAlign - 1) / kAlign * kAlign;
@@ -534,17 +532,14 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
       hj[i].coeffs = reinterpret_cast<const double*>(base + coeff_off[i]);
     dblob = static_cast<char*>(ex.upload(blob));
   }
-  ex.before("axis_table_kernel");
-  if (!ex.dry) {
-    launch_axis_tables(reinterpret_cast<const AxisTableJob*>(dblob + tj_off), (int)tjobs.size(),
-                       ttotal, x64, x32, ex.s);
+  const PlotJob* djobs = reinterpret_cast<const PlotJob*>(dblob + jobs_off);
+  if (prep_items > 0) {
+    ex.before("plot_prep_kernel");
+    if (!ex.dry) launch_plot_prep(djobs, nrel, prep_items, ex.s);
+    ex.launched("plot_prep_kernel");
   }
-  ex.launched("axis_table_kernel");
   ex.before("plot_kernel");
-  if (!ex.dry) {
-    launch_plot(reinterpret_cast<const PlotJob*>(dblob + jobs_off), nrel, tiles, max_rows,
-                max_deg, common_deg, max_res_last, ex.s);
-  }
+  if (!ex.dry) launch_plot(djobs, nrel, tiles, max_rows, max_deg, common_deg, max_res_last, ex.s);
   ex.launched("plot_kernel");
   return plots;
 }

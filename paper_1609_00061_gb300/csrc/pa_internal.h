@@ -19,14 +19,24 @@ constexpr int kMaxDeg = PA_MAX_DEGREE;
 // One relation to plot.  Coefficients are in "nest order": the order in which
 // the nested evaluation visits the monomials (last port outermost, every
 // exponent ascending), so the device reads them front to back.
+//
+// Pixel centres are computed on the device as lo + ((double)i + 0.5) * delta
+// with delta = (hi - lo) / res divided on the host (IEEE division is correctly
+// rounded on both, so the value is the one pa.h defines).
 struct PlotJob {
   const double* coeffs;             // device, nest order
   uint64_t* out;                    // device, pa_array layout
-  const double* x64[kMaxDim];       // per port: FP64 pixel centres of its variable
-  const float* x32_last;            // FP32 copies of the last port's centres
+  double lo[kMaxDim];               // per port: range start of its variable
+  double delta[kMaxDim];            // per port: pixel width of its variable
+  // per-row data written by the preparation kernel (hoisted jobs only)
+  double* g64;                      // [nrows][D+1] row polynomial in the last port
+  float* g32;                       // [nrows][D+1] its FP32 copy
+  float* thr;                       // [nrows][2] FP32 thresholds eps -+ B_row
+  float* y32;                       // [res_last] FP32 centres of the last port
   int64_t nrows;                    // rows = product of all but the last array axis
   int64_t row_words;                // ceil(res_last / 64)
-  int64_t tile0;                    // first block of this job in the launch
+  int64_t tile0;                    // first block of this job in the plot launch
+  int64_t prep0;                    // first item of this job in the preparation launch
   int32_t rows_per_tile;
   int32_t arity, degree, kind, strict;
   int32_t hoisted;                  // 1: the last port is the last array axis, used once
@@ -35,21 +45,15 @@ struct PlotJob {
   int32_t port_axis[kMaxDim];       // port -> array axis
   double eps;
   float eps32;                      // eps rounded to FP32
-  float kfac;                       // FP32 filter: error bound factor on sum |g_j y^j|
+  float kfac;                       // FP32 filter: error bound factor on sum |g_j| Y^j
   float abs_margin;                 // FP32 filter: margin for eps rounding / underflow
   float ymax;                       // >= |y| for every FP32 centre of the last port
   int32_t block_off[kMaxDeg + 1];   // nest-order offset of the coefficients with e_last = j
 };
 
-// Centre tables: x64[off_v + i] = lo_v + ((double)i + 0.5) * ((hi_v - lo_v) / res_v).
-struct AxisTableJob {
-  double lo, hi;
-  int32_t res;
-  int64_t off;
-};
-
-void launch_axis_tables(const AxisTableJob* d_jobs, int njobs, int64_t total, double* x64,
-                        float* x32, cudaStream_t s);
+// prep: per-row polynomials and thresholds, FP32 centre tables (one item per
+// row and one per last-axis pixel of every hoisted job); plot: the pixels.
+void launch_plot_prep(const PlotJob* d_jobs, int njobs, int64_t total_items, cudaStream_t s);
 // common_degree: the degree shared by every job (selects a specialised kernel),
 // or -1 when they differ
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,

@@ -4,51 +4,29 @@
 // PA_LE, f < eps for PA_LT; strict makes every test "<").  The decision is
 // defined by the IEEE double evaluation fixed in pa.h.  GB300 runs FP64 at a
 // small fraction of its FP32 rate, so each pixel is first evaluated in FP32
-// together with a rigorous bound on |f32 - f64|; only pixels whose FP32 value
-// lies within that bound of eps are evaluated again in FP64.  The result is
-// therefore the FP64 decision, bit for bit.
+// against a rigorous bound on |f32 - f64|; only pixels whose FP32 value lies
+// within that bound of eps are evaluated again in FP64.  The result is the
+// FP64 decision, bit for bit.
 //
-// Error bound (row-hoisted evaluation, f = sum_j g_j y^j, y the last port):
-//   g_j are computed once per row in FP64 (exactly as the nested evaluation
-//   does) and rounded to FP32; y32 = fl32(y64).  Then
-//   |f32 - f64| <= (2D+1) u a + (D+1) u a + (2D+1) u64 a  (u = 2^-24),
-//   a = sum_j |g_j| |y|^j, from the FP32 evaluation error, the rounding of
-//   g_j and y, and the FP64 evaluation error.  The kernel uses
-//   B = (4D + 8) u * 1.01 * a32 + 2^-21 eps + 1e-30, which also covers the
-//   rounding of a32, of eps to FP32 and of the comparisons themselves.
+// Row hoisting: with every port but the last fixed, f is a polynomial
+// f = sum_j g_j y^j in the last port y.  The g_j are exactly the inner nested
+// sums of the pa.h evaluation order, so computing them once per row in FP64
+// and finishing each pixel with sum_j g_j y^j performs the very same IEEE
+// operations as evaluating the pixel from scratch.
+//
+// Error bound for the FP32 pass (u = 2^-24, D the degree, g_j rounded to FP32,
+// y32 = fl32(y64), a = sum_j |g_j| |y|^j):
+//   |f32 - f64| <= (2D+1) u a   (FP32 evaluation)
+//               +  (D+1) u a    (rounding of g_j and y)
+//               +  (2D+1) 2^-53 a (FP64 evaluation)
+// and a <= a_row = sum_j |g_j| Y^j with Y >= |y| on the whole axis.  The kernel
+// uses B_row = (4D + 8) u 1.01 a_row + 2^-21 eps + 1e-30, which also covers the
+// rounding of a_row, of eps to FP32 and of the thresholds themselves.
 #include <float.h>
 
 #include "pa_internal.h"
 
 namespace pa {
-
-// ---------------------------------------------------------------- centres
-__global__ void axis_table_kernel(const AxisTableJob* __restrict__ jobs, int njobs, int64_t total,
-                                  double* __restrict__ x64, float* __restrict__ x32) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].off <= g) lo = mid; else hi = mid - 1;
-    }
-    const AxisTableJob j = jobs[lo];
-    const int64_t i = g - j.off;
-    const double delta = __ddiv_rn(__dsub_rn(j.hi, j.lo), (double)j.res);
-    const double t = __dadd_rn((double)i, 0.5);
-    const double x = __dadd_rn(j.lo, __dmul_rn(t, delta));
-    x64[g] = x;
-    x32[g] = __double2float_rn(x);
-  }
-}
-
-void launch_axis_tables(const AxisTableJob* d_jobs, int njobs, int64_t total, double* x64,
-                        float* x32, cudaStream_t s) {
-  if (total <= 0) return;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  axis_table_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total, x64, x32);
-}
 
 // -------------------------------------------------------- nested evaluation
 // sum_{e_k = 0}^{rem} nest(k-1, rem - e_k) * x_k^{e_k}; coefficients are read
@@ -64,6 +42,10 @@ __device__ double nest_dev(int k, int rem, const double*& cp, const double* x) {
   return s;
 }
 
+__device__ __forceinline__ double centre(double lo, double delta, int64_t i) {
+  return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), delta));
+}
+
 __device__ __forceinline__ bool decide64(double f, int kind, double eps, int strict) {
   if (!isfinite(f)) return false;
   if (kind == PA_EQ) {
@@ -73,24 +55,6 @@ __device__ __forceinline__ bool decide64(double f, int kind, double eps, int str
   if (kind == PA_LE) return strict ? (f < eps) : (f <= eps);
   return f < eps;
 }
-
-// --------------------------------------------------------------- plot kernel
-// One block plots a tile of rows (all axes but the last fixed):
-//   A1. thread (r, j) computes the row polynomial's coefficient g_j in FP64
-//       (the inner nested sums, exactly as pa.h orders them) and its FP32 copy;
-//       the FP32 centres of the last axis are copied to shared memory;
-//   A2. thread r bounds the FP32 evaluation error of its row,
-//       B_r = (4D+8) u 1.01 a_r + 2^-21 eps + 1e-30, a_r = sum_j |g_j| Y^j with
-//       Y >= every |y| of the axis, and stores the thresholds eps -+ B_r;
-//   B.  thread per output word: the 64 pixels of the word are evaluated in FP32
-//       (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below eps - B_r is
-//       on, above eps + B_r is off, anything else is decided by the exact FP64
-//       evaluation.  Bits are set directly in the thread's word, so no warp
-//       vote is needed and the row's words are stored coalesced.
-constexpr int kPlotThreads = 256;
-constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
-
-__device__ __forceinline__ int ypad(int i) { return i + (i >> 6); }
 
 // exact FP64 value of sum_j g_j y^j in the order fixed by pa.h
 __device__ __noinline__ bool exact64(double y64, const double* g6, int D, int kind, double eps,
@@ -107,43 +71,100 @@ __device__ __noinline__ bool exact64(double y64, const double* g6, int D, int ki
 __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i) {
   const int ndim = J->ndim;
   int64_t rest = row;
-  int idx[kMaxDim];
-  idx[ndim - 1] = (int)i;
+  int64_t idx[kMaxDim];
+  idx[ndim - 1] = i;
   for (int a = ndim - 2; a >= 0; --a) {
-    idx[a] = (int)(rest % J->res[a]);
+    idx[a] = rest % J->res[a];
     rest /= J->res[a];
   }
   double x[kMaxDim];
-  for (int p = 0; p < J->arity; ++p) x[p] = J->x64[p][idx[J->port_axis[p]]];
+  for (int p = 0; p < J->arity; ++p) x[p] = centre(J->lo[p], J->delta[p], idx[J->port_axis[p]]);
   const double* cp = J->coeffs;
   return decide64(nest_dev(J->arity - 1, J->degree, cp, x), J->kind, J->eps, J->strict);
 }
 
-// g_j of one row: the nested sums over the first arity-1 ports with e_last = j
-__device__ __noinline__ double row_coeff(const PlotJob* J, int64_t row, int j) {
-  const int ndim = J->ndim;
-  int64_t rest = row;
-  int idx[kMaxDim];
-  for (int a = ndim - 2; a >= 0; --a) {
-    idx[a] = (int)(rest % J->res[a]);
-    rest /= J->res[a];
+// ------------------------------------------------------------- preparation
+// Items of job j: rows 0..nrows-1 (row polynomial and thresholds), then the
+// res_last pixels of the last port (FP32 centre table).
+__global__ void __launch_bounds__(256)
+plot_prep_kernel(const PlotJob* __restrict__ jobs, int njobs, int64_t total) {
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].prep0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const PlotJob* J = jobs + lo;
+    const int64_t k = it - J->prep0;
+    const int arity = J->arity, D = J->degree, D1 = D + 1;
+    if (k < J->nrows) {
+      const int64_t row = k;
+      int64_t rest = row;
+      int64_t idx[kMaxDim];
+      for (int a = J->ndim - 2; a >= 0; --a) {
+        idx[a] = rest % J->res[a];
+        rest /= J->res[a];
+      }
+      double x[kMaxDim];
+      for (int p = 0; p < arity - 1; ++p)
+        x[p] = centre(J->lo[p], J->delta[p], idx[J->port_axis[p]]);
+      const double* cp = J->coeffs;
+      const float Y = J->ymax;
+      float a = 0.0f, pw = 1.0f;
+      for (int j = 0; j <= D; ++j) {
+        const double g = nest_dev(arity - 2, D - j, cp, x);  // cp walks block j
+        const float g1 = __double2float_rn(g);
+        J->g64[row * D1 + j] = g;
+        J->g32[row * D1 + j] = g1;
+        a = __fmaf_rn(fabsf(g1), pw, a);
+        pw = __fmul_rn(pw, Y);
+      }
+      const float B = __fmaf_rn(a, J->kfac, J->abs_margin);
+      float tlo = __fsub_rn(J->eps32, B), thi = __fadd_rn(J->eps32, B);
+      if (!(a <= FLT_MAX) || !(B <= FLT_MAX)) {
+        tlo = -INFINITY;  // nothing is certain: every pixel of the row takes the FP64 path
+        thi = INFINITY;
+      }
+      J->thr[2 * row] = tlo;
+      J->thr[2 * row + 1] = thi;
+    } else {
+      const int64_t i = k - J->nrows;
+      J->y32[i] = __double2float_rn(centre(J->lo[arity - 1], J->delta[arity - 1], i));
+    }
   }
-  double x[kMaxDim];
-  for (int p = 0; p < J->arity - 1; ++p) x[p] = J->x64[p][idx[J->port_axis[p]]];
-  const double* cp = J->coeffs + J->block_off[j];
-  return nest_dev(J->arity - 2, J->degree - j, cp, x);
 }
+
+void launch_plot_prep(const PlotJob* d_jobs, int njobs, int64_t total_items, cudaStream_t s) {
+  if (total_items <= 0) return;
+  int64_t blocks = (total_items + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  plot_prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total_items);
+}
+
+// --------------------------------------------------------------- plot kernel
+// One block plots a tile of rows: the FP32 centres of the last axis are staged
+// in shared memory (padded so that consecutive words hit distinct banks), then
+// each thread evaluates whole output words: the 64 pixels of a word in FP32
+// (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below eps - B_row is on,
+// above eps + B_row is off, anything else is decided by the exact FP64
+// evaluation.  Bits are set directly in the thread's word, so no warp vote is
+// needed and a row's words are stored coalesced.
+constexpr int kPlotThreads = 256;
+constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
+
+__device__ __forceinline__ int ypad(int i) { return i + (i >> 6); }
 
 // The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
 // certainly on, bit b of *pending when only the FP64 evaluation can decide.
-template <int DS, bool EQ, bool YS>
+template <int DS, bool EQ, bool YS, bool FULL>
 __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
                                           const float* ytab_w, const float* __restrict__ y32_w,
                                           int nb, uint64_t* on, uint64_t* pending) {
   uint32_t on_lo = 0, on_hi = 0, pe_lo = 0, pe_hi = 0;
 #pragma unroll
   for (int bb = 0; bb < 64; ++bb) {
-    if (bb < nb) {
+    if (FULL || bb < nb) {
       const float y = YS ? ytab_w[bb] : __ldg(y32_w + bb);
       float s = g[0], pw = y;
       if (DS >= 0) {
@@ -174,10 +195,18 @@ __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float
   *pending = ((uint64_t)pe_hi << 32) | pe_lo;
 }
 
+template <int DS, bool EQ, bool YS>
+__device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, float hi,
+                                              const float* ytab_w, const float* y32_w, int nb,
+                                              uint64_t* on, uint64_t* pending) {
+  if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, y32_w, nb, on, pending);
+  else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, y32_w, nb, on, pending);
+}
+
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
-plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int gstride, int rows_cap, int ytab_cap) {
-  extern __shared__ __align__(16) unsigned char smem[];
+plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap) {
+  extern __shared__ __align__(16) float ytab[];
   __shared__ int s_job;
   if (threadIdx.x == 0) {
     int lo = 0, hi = njobs - 1;
@@ -191,86 +220,57 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int gstride, int rows_c
   const PlotJob* J = jobs + s_job;
   const int D = DS >= 0 ? DS : J->degree;
   const int D1 = D + 1;
-  const int arity = J->arity;
   const int row_words = (int)J->row_words;
   const int res_last = J->res[J->ndim - 1];
   const int R = J->rows_per_tile;
   const int64_t row0 = ((int64_t)blockIdx.x - J->tile0) * R;
   const int nr = (int)min((int64_t)R, J->nrows - row0);
-  const int kind = J->kind, strict = J->strict;
-  const double eps = J->eps;
   const bool hoisted = J->hoisted != 0;
-
-  double* g64 = reinterpret_cast<double*>(smem);
-  float* g32 = reinterpret_cast<float*>(g64 + gstride);
-  float* thr = g32 + gstride;                 // [R][2]: eps - B_r, eps + B_r
-  float* ytab = thr + 2 * rows_cap;
-  const bool ysmem = res_last <= ytab_cap;
-  const float* __restrict__ y32g = J->x32_last;
-
-  if (hoisted) {
-    for (int t = threadIdx.x; t < nr * D1; t += blockDim.x) {
-      const int r = t / D1, j = t % D1;
-      const double g = row_coeff(J, row0 + r, j);
-      g64[r * D1 + j] = g;
-      g32[r * D1 + j] = __double2float_rn(g);
-    }
-    if (ysmem)
-      for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = y32g[i];
-    __syncthreads();
-    const float Y = J->ymax, kfac = J->kfac, amarg = J->abs_margin, eps32 = J->eps32;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      float a = 0.0f, pw = 1.0f;
-      for (int j = 0; j <= D; ++j) {
-        a = __fmaf_rn(fabsf(g32[r * D1 + j]), pw, a);
-        pw = __fmul_rn(pw, Y);
-      }
-      const float B = __fmaf_rn(a, kfac, amarg);
-      float lo = __fsub_rn(eps32, B), hi = __fadd_rn(eps32, B);
-      if (!(a <= FLT_MAX) || !(B <= FLT_MAX)) {
-        lo = -INFINITY;   // nothing is certain: every pixel of the row takes the FP64 path
-        hi = INFINITY;
-      }
-      thr[2 * r] = lo;
-      thr[2 * r + 1] = hi;
-    }
+  const bool ysmem = hoisted && res_last <= ytab_cap;
+  const float* __restrict__ y32g = J->y32;
+  if (ysmem) {
+    for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = y32g[i];
     __syncthreads();
   }
-
-  const double* __restrict__ y64t = J->x64[arity - 1];
+  const int kind = J->kind, strict = J->strict;
+  const double eps = J->eps;
+  const double ylo = J->lo[J->arity - 1], ydelta = J->delta[J->arity - 1];
   uint64_t* __restrict__ out = J->out;
   constexpr int kG = DS >= 0 ? DS + 1 : kMaxDeg + 1;
   const int nwords = nr * row_words;
   for (int f = threadIdx.x; f < nwords; f += blockDim.x) {
     const int r = f / row_words, w = f - r * row_words;
+    const int64_t row = row0 + r;
     const int i0 = w * 64;
     const int nb = min(64, res_last - i0);
     uint64_t word = 0;
     if (hoisted) {
       float g[kG];
+      const float* __restrict__ gr = J->g32 + row * D1;
 #pragma unroll
-      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? g32[r * D1 + j] : 0.0f;
-      const float lo = thr[2 * r], hi = thr[2 * r + 1];
+      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? __ldg(gr + j) : 0.0f;
+      const float lo = __ldg(J->thr + 2 * row), hi = __ldg(J->thr + 2 * row + 1);
       uint64_t pending = 0;
       const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
       const float* y32_w = y32g + i0;
       if (kind == PA_EQ) {
-        if (ysmem) eval_word<DS, true, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
-        else eval_word<DS, true, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
       } else {
-        if (ysmem) eval_word<DS, false, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
-        else eval_word<DS, false, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
       }
       while (pending) {
         const int bb = __ffsll((long long)pending) - 1;
         pending &= pending - 1;
-        if (exact64(y64t[i0 + bb], g64 + r * D1, D, kind, eps, strict)) word |= (1ull << bb);
+        if (exact64(centre(ylo, ydelta, i0 + bb), J->g64 + row * D1, D, kind, eps, strict))
+          word |= (1ull << bb);
       }
     } else {
       for (int bb = 0; bb < nb; ++bb)
-        if (general64(J, row0 + r, i0 + bb)) word |= (1ull << bb);
+        if (general64(J, row, i0 + bb)) word |= (1ull << bb);
     }
-    out[(row0 + r) * (int64_t)row_words + w] = word;
+    out[row * row_words + w] = word;
   }
 }
 
@@ -281,18 +281,13 @@ cudaError_t probe_kernel_image() {
 
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, cudaStream_t s) {
+  (void)max_rows_per_tile;
+  (void)max_degree;
   if (total_tiles <= 0) return;
-  const int gstride = max_rows_per_tile * (max_degree + 1);
   const int ycap = max_res_last <= kYTabCap ? max_res_last : 0;
-  const size_t smem = (size_t)gstride * (sizeof(double) + sizeof(float)) +
-                      (size_t)max_rows_per_tile * 2 * sizeof(float) +
-                      (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
+  const size_t smem = (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
   const unsigned grid = (unsigned)total_tiles;
-#define PA_PLOT(DD)                                                                           \
-  do {                                                                                        \
-    cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, gstride, max_rows_per_tile, ycap);           \
-  } while (0)
+#define PA_PLOT(DD) plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, ycap)
   switch (common_degree) {
     case 1: PA_PLOT(1); break;
     case 2: PA_PLOT(2); break;
