@@ -251,8 +251,32 @@ bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end()
 // One two-array cluster (Eq. GAM on X and Y, outer pack `keep`).  When `target`
 // is given (non-null words) and the result lands in its layout, the result is
 // written there directly.
+// Contractions prepared by join() and launched together by flush_rowor().
+struct PendingRowOr {
+  std::vector<RowOrDesc> d;
+};
+
+void flush_rowor(Exec& ex, PendingRowOr& pend) {
+  // one launch per tile width, at most kRowOrMaxBatch contractions each
+  std::vector<int> done(pend.d.size(), 0);
+  for (size_t i = 0; i < pend.d.size(); ++i) {
+    if (done[i]) continue;
+    std::vector<RowOrDesc> group;
+    for (size_t j = i; j < pend.d.size() && (int)group.size() < kRowOrMaxBatch; ++j)
+      if (!done[j] && pend.d[j].Nt == pend.d[i].Nt) {
+        group.push_back(pend.d[j]);
+        done[j] = 1;
+      }
+    ex.before("rowor_kernel");
+    if (!ex.dry) ex.check(launch_rowor(group.data(), (int)group.size(), ex.s), "rowor_kernel");
+    ex.launched("rowor_kernel");
+  }
+  pend.d.clear();
+}
+
 BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
-            const std::vector<int64_t>& vres, const BitArr* target) {
+            const std::vector<int64_t>& vres, const BitArr* target,
+            PendingRowOr* pend = nullptr, int64_t target_ctas = 152) {
   std::vector<int> xv(X.vars, X.vars + X.ndim), yv(Y.vars, Y.vars + Y.ndim);
   double cost = 1.0;
   {
@@ -361,11 +385,15 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
   d.Nw = Bm.row_words();
   d.a_row_words = Am.row_words();
   d.err = ex.ctx->d_err;
-  rowor_plan(d);
+  rowor_plan(d, target_ctas);
   if (d.atomic) ex.memset0(C.w, C.words());
-  ex.before("rowor_kernel");
-  if (!ex.dry) ex.check(launch_rowor(d, ex.s), "rowor_kernel");
-  ex.launched("rowor_kernel");
+  if (pend) {
+    pend->d.push_back(d);
+  } else {
+    PendingRowOr one;
+    one.d.push_back(d);
+    flush_rowor(ex, one);
+  }
   ex.st.peak_words = std::max<int64_t>(ex.st.peak_words, C.words());
   return C;
 }
@@ -570,10 +598,30 @@ void solve_pass(Exec& ex, const SolveArgs& a) {
   BitArr target = from_pa(*a.out);
 
   std::vector<BitArr> slots = plot_all(ex, a.nvars, a.axes, a.nrel, a.rels, a.strict, nullptr);
-  for (size_t t = 0; t < plan.joins.size(); ++t) {
+  // Joins whose inputs are ready at the same time (same depth in the cluster
+  // tree) are independent: their contractions share one launch.
+  const int nj = (int)plan.joins.size();
+  std::vector<int> level(a.nrel + nj, 0);
+  int max_level = 0;
+  for (int t = 0; t < nj; ++t) {
     const Join& jn = plan.joins[t];
-    const bool last = (t + 1 == plan.joins.size());
-    slots.push_back(join(ex, slots[jn.a], slots[jn.b], jn.keep, vres, last ? &target : nullptr));
+    level[a.nrel + t] = 1 + std::max(level[jn.a], level[jn.b]);
+    max_level = std::max(max_level, level[a.nrel + t]);
+  }
+  slots.resize(a.nrel + nj);
+  PendingRowOr pend;
+  for (int lv = 1; lv <= max_level; ++lv) {
+    int n_in_level = 0;
+    for (int t = 0; t < nj; ++t) n_in_level += (level[a.nrel + t] == lv);
+    const int64_t target_ctas = std::max<int64_t>(1, 152 / std::max(1, n_in_level));
+    for (int t = 0; t < nj; ++t) {
+      if (level[a.nrel + t] != lv) continue;
+      const Join& jn = plan.joins[t];
+      const bool last = (t + 1 == nj);
+      slots[a.nrel + t] = join(ex, slots[jn.a], slots[jn.b], jn.keep, vres,
+                               last ? &target : nullptr, &pend, target_ctas);
+    }
+    flush_rowor(ex, pend);
   }
   const BitArr& root = slots[plan.root];
   if (root.w != target.w) reshape(ex, root, target);

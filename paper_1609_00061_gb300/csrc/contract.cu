@@ -125,17 +125,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return false;
 }
 
+struct RowOrMaps {
+  CUtensorMap m[kRowOrMaxBatch];
+};
+struct RowOrBatch {
+  int32_t n;
+  int64_t cta0[kRowOrMaxBatch + 1];
+  RowOrDesc d[kRowOrMaxBatch];
+};
+
 template <int G>
 __global__ void __launch_bounds__(kRowOrThreads)
-rowor_tile_kernel(const __grid_constant__ CUtensorMap tmap, const RowOrDesc d) {
+rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant__ RowOrBatch batch) {
   extern __shared__ __align__(1024) uint64_t bs[];
   const int tid = threadIdx.x;
   const int nwarps = blockDim.x >> 5;
+  int p = 0;
+  while (p + 1 < batch.n && batch.cta0[p + 1] <= (int64_t)blockIdx.x) ++p;
+  const RowOrDesc& d = batch.d[p];
+  const CUtensorMap& tmap = maps.m[p];
   const int64_t staged = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
   uint16_t* lists = reinterpret_cast<uint16_t*>(bs + (staged + 1) * G);
   uint64_t* bar = reinterpret_cast<uint64_t*>(lists + (size_t)nwarps * kListCap);
 
-  int64_t cta = blockIdx.x;
+  int64_t cta = (int64_t)blockIdx.x - batch.cta0[p];
   const int64_t rs = cta % d.row_splits;
   cta /= d.row_splits;
   const int64_t kc = cta % d.k_chunks;
@@ -270,7 +283,7 @@ constexpr size_t kTileBudget = 160 * 1024;  // shared bytes for one B tile (list
 
 }  // namespace
 
-void rowor_plan(RowOrDesc& d) {
+void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
   // widest power-of-two tile (<= 32 words, <= the row) whose K range fits the budget
   int nt_max = 1;
   while (nt_max < 32 && nt_max < d.Nw) nt_max <<= 1;
@@ -291,10 +304,8 @@ void rowor_plan(RowOrDesc& d) {
   d.n_tiles = (d.Nw + Nt - 1) / Nt;
   d.k_chunks = (d.K + d.Kc - 1) / d.Kc;
   d.atomic = d.k_chunks > 1 ? 1 : 0;
-  const size_t smem = rowor_smem_bytes(d);
-  const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(8, (227 * 1024) / (smem + 1024)));
   const int64_t base = d.nbatch * d.n_tiles * d.k_chunks;
-  const int64_t target = 152 * per_sm;
+  const int64_t target = std::max<int64_t>(1, target_ctas);
   int64_t splits = (target + base - 1) / base;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, (d.M + 15) / 16));
   d.rows_per_split = (d.M + splits - 1) / splits;
@@ -306,32 +317,47 @@ size_t rowor_smem_bytes(const RowOrDesc& d) {
   return (size_t)(rows + 1) * d.Nt * 8 + (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16;
 }
 
-cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s) {
-  const int64_t grid = d.nbatch * d.n_tiles * d.k_chunks * d.row_splits;
+int64_t rowor_ctas(const RowOrDesc& d) { return d.nbatch * d.n_tiles * d.k_chunks * d.row_splits; }
+
+cudaError_t launch_rowor(const RowOrDesc* ds, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kRowOrMaxBatch) return cudaErrorInvalidValue;
+  RowOrMaps maps;
+  RowOrBatch batch;
+  memset(&maps, 0, sizeof maps);
+  memset(&batch, 0, sizeof batch);
+  batch.n = n;
+  size_t smem = 0;
+  const int Nt = ds[0].Nt;
+  for (int p = 0; p < n; ++p) {
+    const RowOrDesc& d = ds[p];
+    if (d.Nt != Nt) return cudaErrorInvalidValue;
+    batch.d[p] = d;
+    batch.cta0[p + 1] = batch.cta0[p] + rowor_ctas(d);
+    smem = std::max(smem, rowor_smem_bytes(d));
+    if (d.use_tma) {
+      const cuuint64_t dims[2] = {(cuuint64_t)d.Nw, (cuuint64_t)(d.nbatch * d.K)};
+      const cuuint64_t strides[1] = {(cuuint64_t)d.Nw * 8};
+      const cuuint32_t box[2] = {(cuuint32_t)d.Nt, 256u};
+      const cuuint32_t estr[2] = {1u, 1u};
+      CUresult r = encode_fn()(&maps.m[p], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+                               const_cast<uint64_t*>(d.B), dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+  }
+  const int64_t grid = batch.cta0[n];
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  CUtensorMap tmap;
-  memset(&tmap, 0, sizeof tmap);
-  if (d.use_tma) {
-    const cuuint64_t dims[2] = {(cuuint64_t)d.Nw, (cuuint64_t)(d.nbatch * d.K)};
-    const cuuint64_t strides[1] = {(cuuint64_t)d.Nw * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)d.Nt, 256u};
-    const cuuint32_t estr[2] = {1u, 1u};
-    CUresult r = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
-                             const_cast<uint64_t*>(d.B), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  }
-  const size_t smem = rowor_smem_bytes(d);
 #define PA_ROWOR(GG)                                                                         \
   do {                                                                                       \
     cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          (int)smem);                                                         \
-    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(tmap, d);                        \
+    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(maps, batch);          \
   } while (0)
-  switch (d.Nt) {
+  switch (Nt) {
     case 1: PA_ROWOR(1); break;
     case 2: PA_ROWOR(2); break;
     case 4: PA_ROWOR(4); break;

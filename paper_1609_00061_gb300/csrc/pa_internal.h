@@ -121,10 +121,15 @@ struct RowOrDesc {
   int32_t use_tma;            // 1: stage the tile with cp.async.bulk.tensor
   int* err;                   // device error word: set when a bounded wait runs out
 };
-// Choose the tile shape and grid for a contraction of this shape.
-void rowor_plan(RowOrDesc& d);
+// Choose the tile shape and grid for a contraction of this shape; the grid
+// aims at about target_ctas CTAs (several contractions can share one launch).
+void rowor_plan(RowOrDesc& d, int64_t target_ctas);
 size_t rowor_smem_bytes(const RowOrDesc& d);
-cudaError_t launch_rowor(const RowOrDesc& d, cudaStream_t s);
+constexpr int kRowOrMaxBatch = 16;
+// Independent contractions with the same tile width Nt in one launch
+// (n <= kRowOrMaxBatch).
+cudaError_t launch_rowor(const RowOrDesc* d, int n, cudaStream_t s);
+int64_t rowor_ctas(const RowOrDesc& d);
 // cudaSuccess when this build holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);

@@ -144,6 +144,8 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
   }
   std::vector<int> live;
   for (int i = 0; i < nrel; ++i) live.push_back(i);
+  // depth of every slot in the cluster tree (plots 0)
+  std::vector<int> depth(nrel, 0);
   (void)nvars;
   auto needed_outside = [&](const std::vector<int>& skip) {
     std::vector<int> need = exposed;
@@ -170,17 +172,24 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
       a = live[0];
       b = live[1];
     } else {
+      // smallest result, then smallest cost r^Lambda, then the shallower pair:
+      // among equal joins the tree stays balanced, so that independent joins
+      // can run side by side (the parallel cost of Sec. 3.5)
       double best_size = 0, best_cost = 0;
+      int best_depth = 0;
       for (size_t i = 0; i < live.size(); ++i)
         for (size_t j = i + 1; j < live.size(); ++j) {
           int x = live[i], y = live[j];
           double size = set_size(keep_of(x, y), vres);
           double cost = set_size(set_union(slot_vars[x], slot_vars[y]), vres);
-          if (a < 0 || size < best_size || (size == best_size && cost < best_cost)) {
+          int dep = std::max(depth[x], depth[y]);
+          if (a < 0 || size < best_size || (size == best_size && cost < best_cost) ||
+              (size == best_size && cost == best_cost && dep < best_depth)) {
             a = x;
             b = y;
             best_size = size;
             best_cost = cost;
+            best_depth = dep;
           }
         }
     }
@@ -194,6 +203,7 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
     plan.peak_bits = std::max(plan.peak_bits, set_size(jn.keep, vres));
     int id = nrel + t;
     slot_vars.push_back(jn.keep);
+    depth.push_back(1 + std::max(depth[a], depth[b]));
     live.erase(std::find(live.begin(), live.end(), a));
     live.erase(std::find(live.begin(), live.end(), b));
     live.insert(live.begin(), id);

@@ -42,6 +42,33 @@ __device__ double nest_dev(int k, int rem, const double*& cp, const double* x) {
   return s;
 }
 
+// The same sum with the depth known at compile time (no call stack): used for
+// the row polynomials, K = arity - 2.
+template <int K>
+__device__ __forceinline__ double nest_t(int rem, const double*& cp, const double* x) {
+  if constexpr (K < 0) {
+    return *cp++;
+  } else {
+    double s = 0.0, pw = 1.0;
+    for (int e = 0; e <= rem; ++e) {
+      const double term = __dmul_rn(nest_t<K - 1>(rem - e, cp, x), pw);
+      s = (e == 0) ? term : __dadd_rn(s, term);
+      pw = __dmul_rn(pw, x[K]);
+    }
+    return s;
+  }
+}
+
+__device__ __forceinline__ double nest_rows(int k, int rem, const double*& cp, const double* x) {
+  switch (k) {
+    case -1: return nest_t<-1>(rem, cp, x);
+    case 0: return nest_t<0>(rem, cp, x);
+    case 1: return nest_t<1>(rem, cp, x);
+    case 2: return nest_t<2>(rem, cp, x);
+    default: return nest_dev(k, rem, cp, x);
+  }
+}
+
 __device__ __forceinline__ double centre(double lo, double delta, int64_t i) {
   return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), delta));
 }
@@ -113,7 +140,7 @@ plot_prep_kernel(const PlotJob* __restrict__ jobs, int njobs, int64_t total) {
       const float Y = J->ymax;
       float a = 0.0f, pw = 1.0f;
       for (int j = 0; j <= D; ++j) {
-        const double g = nest_dev(arity - 2, D - j, cp, x);  // cp walks block j
+        const double g = nest_rows(arity - 2, D - j, cp, x);  // cp walks block j
         const float g1 = __double2float_rn(g);
         J->g64[row * D1 + j] = g;
         J->g32[row * D1 + j] = g1;
