@@ -204,33 +204,51 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
   constexpr int P = 32 / G;
   uint16_t* list = lists + (size_t)warp * kListCap;
   // rows are dealt out cyclically over every warp of the CTAs sharing this
-  // tile, so that runs of dense rows (curves are locally thick) are spread out
+  // tile, so that runs of dense rows (curves are locally thick) are spread out.
+  // A warp's work is a sequence of units (row, batch of 32 A words); the A
+  // words of the next four units are always in flight while one is processed.
   const int64_t gw = rs * nwarps + warp;
   const int64_t gstride = d.row_splits * nwarps;
   const int64_t kw0 = k0 / 64;
   const int64_t kw1 = min(d.a_row_words, (k0 + kc_len + 63) / 64);
-  for (int64_t m = gw; m < d.M; m += gstride) {
-    const int64_t row = b * d.M + m;
-    const uint64_t* __restrict__ arow = d.A + row * d.a_row_words;
-    uint64_t acc = 0;
-    for (int64_t wb = kw0; wb < kw1; wb += 32) {
-      const int64_t kwl = wb + lane;
-      uint64_t a = (kwl < kw1) ? __ldg(arow + kwl) : 0ull;
-      const int c = __popcll(a);
-      int incl = c;
+  const int64_t nbat = (kw1 - kw0 + 31) / 32;
+  const int64_t nrows_w = (gw < d.M) ? (d.M - gw + gstride - 1) / gstride : 0;
+  const int64_t nunits = nrows_w * nbat;
+  const uint64_t* __restrict__ abase = d.A + (b * d.M) * d.a_row_words;
+  auto load_unit = [&](int64_t u) -> uint64_t {
+    if (u >= nunits) return 0ull;
+    const int64_t i = u / nbat, q = u - i * nbat;
+    const int64_t m = gw + i * gstride;
+    const int64_t kwl = kw0 + q * 32 + lane;
+    return (kwl < kw1) ? __ldg(abase + m * d.a_row_words + kwl) : 0ull;
+  };
+  uint64_t pre0 = load_unit(0), pre1 = load_unit(1), pre2 = load_unit(2), pre3 = load_unit(3);
+  uint64_t acc = 0;
+  for (int64_t u = 0; u < nunits; ++u) {
+    uint64_t a = pre0;
+    pre0 = pre1;
+    pre1 = pre2;
+    pre2 = pre3;
+    pre3 = load_unit(u + 4);
+    const int64_t i = u / nbat, q = u - i * nbat;
+    if (q == 0) acc = 0;
+    const int64_t kwl = kw0 + q * 32 + lane;
+    const int c = __popcll(a);
+    int incl = c;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const int T = __shfl_sync(0xffffffffu, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int T = __shfl_sync(0xffffffffu, incl, 31);
+    if (T > 0) {
       int off = incl - c;
       const int base = (int)(kwl * 64 - k0);
       while (a) {
         const int bit = __ffsll((long long)a) - 1;
         a &= a - 1;
-        const int i = base + bit;
-        list[off++] = (uint16_t)(i < kc_len ? i : kc_len);
+        const int ix = base + bit;
+        list[off++] = (uint16_t)(ix < kc_len ? ix : kc_len);
       }
       __syncwarp();
       for (int e = grp; e < T; e += 4 * P) {
@@ -243,19 +261,27 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
       }
       __syncwarp();
     }
+    if (q == nbat - 1) {
+      uint64_t r = acc;
 #pragma unroll
-    for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
-    const int64_t n = n0 + lane;
-    if (lane < G && n < d.Nw) {
-      uint64_t* c = d.C + row * d.Nw + n;
-      if (d.atomic) {
-        if (acc) atomicOr((unsigned long long*)c, (unsigned long long)acc);
-      } else {
-        *c = acc;
+      for (int o = G; o < 32; o <<= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
+      const int64_t m = gw + i * gstride;
+      const int64_t n = n0 + lane;
+      if (lane < G && n < d.Nw) {
+        uint64_t* c = d.C + (b * d.M + m) * d.Nw + n;
+        if (d.atomic) {
+          if (r) atomicOr((unsigned long long*)c, (unsigned long long)r);
+        } else {
+          *c = r;
+        }
       }
     }
   }
 }
+
+}  // namespace
+
+namespace {
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
