@@ -101,7 +101,7 @@ void launch_reshape(const ReshapeDesc& d, cudaStream_t s) {
 namespace {
 
 constexpr int kRowOrThreads = 512;
-constexpr int kListCap = 32 * 64;  // one batch of 32 A words
+constexpr int kListCap = 32 * 64 + 128;  // one batch of 32 A words, plus sentinel padding
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -207,43 +207,42 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
   // tile, so that runs of dense rows (curves are locally thick) are spread out.
   // A warp's work is a sequence of units (row, batch of 32 A words); the A
   // words of the next four units are always in flight while one is processed.
-  const int64_t gw = rs * nwarps + warp;
-  const int64_t gstride = d.row_splits * nwarps;
-  const int64_t kw0 = k0 / 64;
-  const int64_t kw1 = min(d.a_row_words, (k0 + kc_len + 63) / 64);
-  const int64_t nbat = (kw1 - kw0 + 31) / 32;
-  const int64_t nrows_w = (gw < d.M) ? (d.M - gw + gstride - 1) / gstride : 0;
-  const int64_t nunits = nrows_w * nbat;
+  const int gw = (int)rs * nwarps + warp;
+  const int gstride = (int)d.row_splits * nwarps;
+  const int kw0 = (int)(k0 / 64);
+  const int kw1 = (int)min(d.a_row_words, (k0 + kc_len + 63) / 64);
+  const int nbat = (kw1 - kw0 + 31) / 32;
+  const int M = (int)d.M;
+  const int nrows_w = (gw < M) ? (M - gw + gstride - 1) / gstride : 0;
+  const int nunits = nrows_w * nbat;
   const uint64_t* __restrict__ abase = d.A + (b * d.M) * d.a_row_words;
-  auto load_unit = [&](int64_t u) -> uint64_t {
+  const int64_t arw = d.a_row_words;
+  int* wcount = reinterpret_cast<int*>(bar + 1) + warp;
+  if (lane == 0) *wcount = 0;
+  __syncwarp();
+  auto load_unit = [&](int u) -> uint64_t {
     if (u >= nunits) return 0ull;
-    const int64_t i = u / nbat, q = u - i * nbat;
-    const int64_t m = gw + i * gstride;
-    const int64_t kwl = kw0 + q * 32 + lane;
-    return (kwl < kw1) ? __ldg(abase + m * d.a_row_words + kwl) : 0ull;
+    const int i = (nbat == 1) ? u : u / nbat;
+    const int q = u - i * nbat;
+    const int kwl = kw0 + q * 32 + lane;
+    return (kwl < kw1) ? __ldg(abase + (int64_t)(gw + i * gstride) * arw + kwl) : 0ull;
   };
   uint64_t pre0 = load_unit(0), pre1 = load_unit(1), pre2 = load_unit(2), pre3 = load_unit(3);
   uint64_t acc = 0;
-  for (int64_t u = 0; u < nunits; ++u) {
+  for (int u = 0; u < nunits; ++u) {
     uint64_t a = pre0;
     pre0 = pre1;
     pre1 = pre2;
     pre2 = pre3;
     pre3 = load_unit(u + 4);
-    const int64_t i = u / nbat, q = u - i * nbat;
+    const int i = (nbat == 1) ? u : u / nbat;
+    const int q = u - i * nbat;
     if (q == 0) acc = 0;
-    const int64_t kwl = kw0 + q * 32 + lane;
-    const int c = __popcll(a);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int T = __shfl_sync(0xffffffffu, incl, 31);
-    if (T > 0) {
-      int off = incl - c;
-      const int base = (int)(kwl * 64 - k0);
+    if (__any_sync(0xffffffffu, a != 0ull)) {
+      // list of the set bits (tile-row indices), in any order
+      const int c = __popcll(a);
+      int off = c ? atomicAdd(wcount, c) : 0;
+      const int base = (kw0 + q * 32 + lane) * 64 - (int)k0;
       while (a) {
         const int bit = __ffsll((long long)a) - 1;
         a &= a - 1;
@@ -251,21 +250,23 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
         list[off++] = (uint16_t)(ix < kc_len ? ix : kc_len);
       }
       __syncwarp();
+      const int T = *wcount;
+      // pad to a whole number of rounds with the sentinel row
+      if (lane < 4 * P) list[T + lane] = (uint16_t)kc_len;
+      __syncwarp();
       for (int e = grp; e < T; e += 4 * P) {
-        const int i0 = list[e];
-        const int i1 = (e + P < T) ? list[e + P] : kc_len;
-        const int i2 = (e + 2 * P < T) ? list[e + 2 * P] : kc_len;
-        const int i3 = (e + 3 * P < T) ? list[e + 3 * P] : kc_len;
-        acc |= bs[(size_t)i0 * G + lig] | bs[(size_t)i1 * G + lig] | bs[(size_t)i2 * G + lig] |
-               bs[(size_t)i3 * G + lig];
+        const int i0 = list[e], i1 = list[e + P], i2 = list[e + 2 * P], i3 = list[e + 3 * P];
+        acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
       }
+      __syncwarp();
+      if (lane == 0) *wcount = 0;
       __syncwarp();
     }
     if (q == nbat - 1) {
       uint64_t r = acc;
 #pragma unroll
       for (int o = G; o < 32; o <<= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
-      const int64_t m = gw + i * gstride;
+      const int m = gw + i * gstride;
       const int64_t n = n0 + lane;
       if (lane < G && n < d.Nw) {
         uint64_t* c = d.C + (b * d.M + m) * d.Nw + n;
@@ -305,7 +306,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-constexpr size_t kTileBudget = 160 * 1024;  // shared bytes for one B tile (lists: 64 KB more)
+constexpr size_t kTileBudget = 156 * 1024;  // shared bytes for one B tile (the lists take 68 KB more)
 
 }  // namespace
 
@@ -340,7 +341,8 @@ void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
 
 size_t rowor_smem_bytes(const RowOrDesc& d) {
   const int64_t rows = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
-  return (size_t)(rows + 1) * d.Nt * 8 + (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16;
+  return (size_t)(rows + 1) * d.Nt * 8 + (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16 +
+         (size_t)(kRowOrThreads / 32) * 4;
 }
 
 int64_t rowor_ctas(const RowOrDesc& d) { return d.nbatch * d.n_tiles * d.k_chunks * d.row_splits; }
