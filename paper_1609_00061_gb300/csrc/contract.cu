@@ -251,8 +251,9 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
       }
       __syncwarp();
       const int T = *wcount;
-      // pad to a whole number of rounds with the sentinel row
-      if (lane < 4 * P) list[T + lane] = (uint16_t)kc_len;
+      // pad to a whole number of rounds with the sentinel row (4P entries,
+      // which is more than one per lane when the groups are narrow)
+      for (int t = lane; t < 4 * P; t += 32) list[T + t] = (uint16_t)kc_len;
       __syncwarp();
       for (int e = grp; e < T; e += 4 * P) {
         const int i0 = list[e], i1 = list[e + P], i2 = list[e + 2 * P], i3 = list[e + 3 * P];
