@@ -157,7 +157,9 @@ pa_status pa_sync(pa_ctx* ctx, void* stream);
  * waits for those events, adds the elapsed times up per kernel name and clears
  * the record.  names receives up to max_kernels NUL-terminated names of at most
  * 31 characters, 32 bytes apart; launches[k] and total_ms[k] the count and the
- * summed milliseconds of kernel k; *nkernels the number of distinct kernels. */
+ * summed milliseconds of kernel k; *nkernels the number of distinct kernels.
+ * The last entry is not a kernel: "words_or", whose launches field counts the
+ * 64-bit words the contraction kernels OR-ed while timing was on. */
 pa_status pa_profile_enable(pa_ctx* ctx, int32_t on);
 pa_status pa_profile_read(pa_ctx* ctx, int32_t max_kernels, char* names, int64_t* launches,
                           double* total_ms, int32_t* nkernels);

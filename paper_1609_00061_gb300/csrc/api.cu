@@ -29,6 +29,7 @@ struct pa_ctx {
   std::string err;
   // kernel timing (pa_profile_enable)
   int* d_err = nullptr;  // device error word written by bounded waits
+  unsigned long long* d_stat = nullptr;  // words OR-ed by contractions (timing mode)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
@@ -385,6 +386,7 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
   d.Nw = Bm.row_words();
   d.a_row_words = Am.row_words();
   d.err = ex.ctx->d_err;
+  d.stat = ex.ctx->prof ? ex.ctx->d_stat : nullptr;
   rowor_plan(d, target_ctas);
   if (d.atomic) ex.memset0(C.w, C.words());
   if (pend) {
@@ -702,10 +704,13 @@ pa_status pa_create(pa_ctx** out, int device, size_t workspace_cap) {
   ctx->cap = workspace_cap;
   if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_err), sizeof(int)) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_stat), sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->d_stat, 0, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_stat) cudaFree(ctx->d_stat);
     delete ctx;
     return PA_ERR_CUDA;
   }
@@ -719,6 +724,7 @@ void pa_destroy(pa_ctx* ctx) {
   if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_done);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->d_stat) cudaFree(ctx->d_stat);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -759,6 +765,13 @@ pa_status pa_profile_read(pa_ctx* ctx, int32_t max_kernels, char* names, int64_t
   }
   ctx->recs.clear();
   ctx->ev_used = 0;
+  unsigned long long words = 0;
+  cudaError_t e2 = cudaMemcpy(&words, ctx->d_stat, sizeof words, cudaMemcpyDeviceToHost);
+  if (e2 != cudaSuccess) return set_err(ctx, PA_ERR_CUDA, cudaGetErrorString(e2));
+  cudaMemset(ctx->d_stat, 0, sizeof words);
+  seen.push_back("words_or");  // not a kernel: 64-bit words OR-ed by the contractions
+  cnt.push_back((int64_t)words);
+  tot.push_back(0.0);
   *nkernels = (int32_t)seen.size();
   for (int k = 0; k < (int)seen.size() && k < max_kernels; ++k) {
     snprintf(names + 32 * k, 32, "%s", seen[k].c_str());

@@ -260,7 +260,10 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
         acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
       }
       __syncwarp();
-      if (lane == 0) *wcount = 0;
+      if (lane == 0) {
+        *wcount = 0;
+        if (d.stat) atomicAdd(d.stat, (unsigned long long)T * G);
+      }
       __syncwarp();
     }
     if (q == nbat - 1) {

@@ -120,6 +120,7 @@ struct RowOrDesc {
   int32_t atomic;             // 1: C pre-zeroed, results OR-ed in atomically
   int32_t use_tma;            // 1: stage the tile with cp.async.bulk.tensor
   int* err;                   // device error word: set when a bounded wait runs out
+  unsigned long long* stat;   // when not null: += shared-memory words OR-ed (timing mode)
 };
 // Choose the tile shape and grid for a contraction of this shape; the grid
 // aims at about target_ctas CTAs (several contractions can share one launch).
