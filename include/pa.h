@@ -140,7 +140,20 @@ typedef struct {
   int64_t workspace_bytes;   /* workspace in use by the call */
 } pa_stats;
 
+/* One independent system for the batched entry points: its own variables,
+ * boxes, relations and exposed set (same meaning as pa_solve_network's
+ * arguments; all pointers are host pointers). */
+typedef struct {
+  int32_t nvars;
+  const pa_axis* axes;
+  int32_t nrel;
+  const pa_relation* rels;
+  int32_t nexposed;
+  const int32_t* exposed;
+} pa_system;
+
 typedef struct pa_ctx pa_ctx;
+typedef struct pa_batch pa_batch;
 
 /* Create a context on `device`.  workspace_cap bounds the scratch memory the
  * context may hold (0: no bound).  Returns PA_ERR_CUDA when the device cannot
@@ -200,6 +213,26 @@ pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int3
                            const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
                            const pa_options* opts, pa_array* out, pa_stats* stats,
                            void* stream);
+
+/* Many independent systems at once (Sec. 3.6 applied to each): all plots in
+ * one launch pair, and the joins of equal depth in all the systems' cluster
+ * trees in one contraction launch per tile width.  outs[k] receives system k's
+ * array over its exposed variables.  opts->order must not be PA_ORDER_GIVEN. */
+pa_status pa_solve_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
+                         const pa_options* opts, pa_stats* stats, void* stream);
+
+/* A planned batch: the same work as pa_solve_batch, planned once into the
+ * batch's own device memory and captured as one CUDA graph (the host-to-device
+ * copy of every descriptor and coefficient, then every launch).  pa_batch_run
+ * replays it on `stream`; the outputs and the coefficients are those given to
+ * pa_batch_create, whose host arrays may be freed after it returns.  A batch
+ * must not run concurrently with itself.  pa_batch_destroy waits for the
+ * device before freeing its memory. */
+pa_status pa_batch_create(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
+                          const pa_options* opts, pa_batch** batch);
+pa_status pa_batch_run(pa_batch* batch, void* stream);
+pa_status pa_batch_stats(const pa_batch* batch, pa_stats* stats);
+void pa_batch_destroy(pa_batch* batch);
 
 /* The join order pa_solve_network would use (host only, no GPU): writes
  * 2*(nrel-1) slot indices into pairs_out (same numbering as pa_options.pairs). */

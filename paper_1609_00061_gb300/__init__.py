@@ -19,7 +19,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native
-from ._native import PaArray, PaAxis, PaOptions, PaRelation, PaStats
+from ._native import PaArray, PaAxis, PaOptions, PaRelation, PaStats, PaSystem
 
 PA_OK = 0
 STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
@@ -181,6 +181,78 @@ def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pa
     return st.as_dict()
 
 
+def _systems(systems):
+    """Marshal workloads.System objects; returns (array, keep-alive list)."""
+    arr = (PaSystem * len(systems))()
+    keep = []
+    for k, sy in enumerate(systems):
+        ax = _axes(sy.axes)
+        rl, kc = _relations(sy.rels)
+        ex = _i32(sy.exposed)
+        keep.extend([ax, rl, kc, ex])
+        arr[k].nvars = len(sy.axes)
+        arr[k].axes = ctypes.cast(ax, ctypes.POINTER(PaAxis))
+        arr[k].nrel = len(sy.rels)
+        arr[k].rels = ctypes.cast(rl, ctypes.POINTER(PaRelation))
+        arr[k].nexposed = len(sy.exposed)
+        arr[k].exposed = ctypes.cast(ex, ctypes.POINTER(ctypes.c_int32))
+    return arr, keep
+
+
+def _opts(order, strict):
+    opts = PaOptions()
+    opts.strict = int(bool(strict))
+    opts.order = ORDERS[order] if isinstance(order, str) else int(order)
+    return opts
+
+
+def pa_solve_batch(ctx, systems, outs, order="greedy", strict=False, stream=None) -> dict:
+    """Solve many independent workloads.System objects in shared launches."""
+    arr, keep = _systems(systems)
+    oc = (PaArray * len(outs))(*[o.c() for o in outs])
+    st = PaStats()
+    _check(_lib().pa_solve_batch(ctx, len(systems), arr, oc, ctypes.byref(_opts(order, strict)),
+                                 ctypes.byref(st), _stream_ptr(stream)), ctx)
+    return st.as_dict()
+
+
+class Batch:
+    """A planned batch captured as one CUDA graph (pa_batch_create / pa_batch_run)."""
+
+    def __init__(self, engine, systems, outs=None, order="greedy", strict=False):
+        self.engine = engine
+        if outs is None:
+            outs = [BitArray.empty(sy.exposed, [sy.axes[v][2] for v in sy.exposed], engine.device)
+                    for sy in systems]
+        self.outs = outs
+        arr, keep = _systems(systems)
+        oc = (PaArray * len(outs))(*[o.c() for o in outs])
+        h = ctypes.c_void_p()
+        _check(_lib().pa_batch_create(engine.ctx, len(systems), arr, oc,
+                                      ctypes.byref(_opts(order, strict)), ctypes.byref(h)),
+               engine.ctx)
+        self.h = h
+
+    def run(self, stream=None):
+        _check(_lib().pa_batch_run(self.h, _stream_ptr(stream)), self.engine.ctx)
+
+    def stats(self) -> dict:
+        st = PaStats()
+        _check(_lib().pa_batch_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            _lib().pa_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def pa_plan_order(axes, rels, exposed, order="greedy"):
     """Join order (list of slot pairs), dense pixel-op count and peak bits; host only."""
     r, keep = _relations(rels)
@@ -275,6 +347,17 @@ class Engine:
         st = pa_solve_network(self.ctx, system.axes, system.rels, system.exposed, out, order,
                               pairs, strict, stream)
         return out, st
+
+    def solve_batch(self, systems, order="greedy", strict=False, stream=None, outs=None):
+        """Solve a list of workloads.System; returns (list of BitArray, stats)."""
+        if outs is None:
+            outs = [BitArray.empty(sy.exposed, [sy.axes[v][2] for v in sy.exposed], self.device)
+                    for sy in systems]
+        st = pa_solve_batch(self.ctx, systems, outs, order, strict, stream)
+        return outs, st
+
+    def batch(self, systems, order="greedy", strict=False, outs=None) -> "Batch":
+        return Batch(self, systems, outs, order, strict)
 
     def sync(self, stream=None):
         pa_sync(self.ctx, stream)

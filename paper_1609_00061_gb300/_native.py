@@ -101,10 +101,17 @@ class PaStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PaSystem(ctypes.Structure):
+    _fields_ = [("nvars", c_i32), ("axes", ctypes.POINTER(PaAxis)), ("nrel", c_i32),
+                ("rels", ctypes.POINTER(PaRelation)), ("nexposed", c_i32),
+                ("exposed", ctypes.POINTER(c_i32))]
+
+
 EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_words",
            "pa_profile_enable", "pa_profile_read",
-           "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_plan_order",
-           "pa_tree_cost"]
+           "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_solve_batch",
+           "pa_batch_create", "pa_batch_run", "pa_batch_stats", "pa_batch_destroy",
+           "pa_plan_order", "pa_tree_cost"]
 
 _lib = None
 
@@ -144,6 +151,16 @@ def load(build_if_missing: bool = True):
     lib.pa_solve_network.argtypes = [vp, c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32),
                                      P(PaOptions), P(PaArray), P(PaStats), vp]
     lib.pa_solve_network.restype = c_i32
+    lib.pa_solve_batch.argtypes = [vp, c_i32, P(PaSystem), P(PaArray), P(PaOptions), P(PaStats), vp]
+    lib.pa_solve_batch.restype = c_i32
+    lib.pa_batch_create.argtypes = [vp, c_i32, P(PaSystem), P(PaArray), P(PaOptions), P(vp)]
+    lib.pa_batch_create.restype = c_i32
+    lib.pa_batch_run.argtypes = [vp, vp]
+    lib.pa_batch_run.restype = c_i32
+    lib.pa_batch_stats.argtypes = [vp, P(PaStats)]
+    lib.pa_batch_stats.restype = c_i32
+    lib.pa_batch_destroy.argtypes = [vp]
+    lib.pa_batch_destroy.restype = None
     lib.pa_plan_order.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32), c_i32,
                                   P(c_i32), P(c_f64), P(c_i64)]
     lib.pa_plan_order.restype = c_i32

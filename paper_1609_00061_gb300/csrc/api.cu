@@ -1,11 +1,13 @@
 // C interface of the pixel array engine (include/pa.h): argument checks, the
-// context and its workspace, and the executor that turns a join plan into
-// kernel launches.
+// context and its workspace, and the builder that turns join plans into a
+// launch program.
 //
-// The executor runs every call twice: a sizing pass that only adds up the
-// workspace it needs (no CUDA calls), then the real pass.  All work of a call is
-// stream-ordered on the caller's stream, so workspace regions are never read
-// after the call's last kernel.
+// Every call is built twice: a sizing pass that only adds up the workspace and
+// the descriptor blob it needs (no CUDA calls), then the real pass, which
+// fills the blob with device addresses and records the launches.  The blob is
+// copied to the device in one transfer and the launches run in order on the
+// caller's stream.  A planned batch (pa_batch_create) keeps its program and its
+// own memory and replays the whole sequence as one CUDA graph.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -27,9 +29,9 @@ struct pa_ctx {
   cudaEvent_t stage_done = nullptr;
   bool stage_pending = false;
   std::string err;
-  // kernel timing (pa_profile_enable)
-  int* d_err = nullptr;  // device error word written by bounded waits
+  int* d_err = nullptr;                  // device error word written by bounded waits
   unsigned long long* d_stat = nullptr;  // words OR-ed by contractions (timing mode)
+  // kernel timing (pa_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
@@ -59,91 +61,74 @@ pa_status set_err(pa_ctx* ctx, pa_status st, const std::string& msg) {
     if (!(cond)) throw Fail{set_err(ctx, PA_ERR_INVALID_ARG, msg)}; \
   } while (0)
 
-// ------------------------------------------------------------ executor
-struct Exec {
-  pa_ctx* ctx;
-  cudaStream_t s;
-  bool dry;
-  size_t used = 0;
-  pa_stats st{};
+bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
-  Exec(pa_ctx* c, cudaStream_t st_, bool dry_) : ctx(c), s(st_), dry(dry_) {}
+// ------------------------------------------------------------ program
+enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR };
+
+struct Op {
+  OpKind kind;
+  size_t off0 = 0, off1 = 0, off2 = 0;  // blob offsets (plot jobs; rowor descs, maps, cta0)
+  int n = 0;                            // plot jobs / rowor problems
+  int64_t count = 0;                    // prep items / plot tiles / rowor grid / words
+  int i0 = 0, i1 = 0, i2 = 0, i3 = 0;   // plot: rows/tile, max degree, common degree, max res
+  size_t smem = 0;                      // rowor dynamic shared memory
+  uint64_t* p = nullptr;                // memset / and output
+  const uint64_t* a = nullptr;
+  const uint64_t* b = nullptr;
+  ReshapeDesc rd;
+};
+
+const char* op_name(const Op& op) {
+  switch (op.kind) {
+    case OP_PREP: return "plot_prep_kernel";
+    case OP_PLOT: return "plot_kernel";
+    case OP_MEMSET: return "memset";
+    case OP_RESHAPE: return "reshape_kernel";
+    case OP_AND: return "and_kernel";
+    default: return "rowor_kernel";
+  }
+}
+
+// Builds the workspace layout, the descriptor blob and the launch list of a call.
+struct Builder {
+  pa_ctx* ctx;
+  bool dry;
+  char* base = nullptr;     // device memory the layout lives in (null in the sizing pass)
+  size_t used = 0;          // bytes of `base` in use
+  size_t blob_cap = 0;      // bytes reserved for the blob at the start of `base`
+  std::vector<char> blob;   // host image of the descriptor blob
+  std::vector<Op> ops;
+  pa_stats st{};
+  int* d_err = nullptr;
+  unsigned long long* d_stat = nullptr;
+  std::vector<RowOrDesc> pend;  // contractions waiting for one shared launch
+
+  Builder(pa_ctx* c, bool dry_, char* base_, size_t blob_cap_)
+      : ctx(c), dry(dry_), base(base_), used(blob_cap_), blob_cap(blob_cap_) {}
 
   void* alloc(size_t bytes) {
     const size_t off = (used + kAlign - 1) / kAlign * kAlign;
     used = off + std::max<size_t>(bytes, 8);
     if (dry) return reinterpret_cast<void*>(static_cast<uintptr_t>(kAlign + off));
-    return ctx->arena + off;
+    return base + off;
   }
   uint64_t* alloc_words(int64_t n) { return static_cast<uint64_t*>(alloc((size_t)n * 8)); }
 
-  void check(cudaError_t e, const char* what) {
-    if (e != cudaSuccess) {
-      throw Fail{set_err(ctx, PA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e))};
-    }
+  template <class T>
+  size_t put(const T* data, size_t n, size_t align = 16) {
+    const size_t off = (blob.size() + align - 1) / align * align;
+    blob.resize(off + sizeof(T) * n);
+    if (n) memcpy(blob.data() + off, data, sizeof(T) * n);
+    return off;
   }
-  cudaEvent_t next_event() {
-    if (ctx->ev_used == ctx->ev_pool.size()) {
-      cudaEvent_t e;
-      check(cudaEventCreate(&e), "cudaEventCreate");
-      ctx->ev_pool.push_back(e);
-    }
-    return ctx->ev_pool[ctx->ev_used++];
+  // device address of a blob offset (fake in the sizing pass)
+  char* dev(size_t off) const {
+    if (dry) return reinterpret_cast<char*>(static_cast<uintptr_t>(64 + off));
+    return base + off;
   }
-  // bracket the next launch with events when timing is on
-  void before(const char* what) {
-    if (dry || !ctx->prof) return;
-    pa_ctx::Rec r;
-    r.name = what;
-    r.a = next_event();
-    r.b = next_event();
-    check(cudaEventRecord(r.a, s), "cudaEventRecord");
-    ctx->recs.push_back(r);
-  }
-  void launched(const char* what) {
-    st.n_launches++;
-    if (dry) return;
-    check(cudaGetLastError(), what);
-    if (ctx->prof && !ctx->recs.empty()) check(cudaEventRecord(ctx->recs.back().b, s), "cudaEventRecord");
-  }
-  void memset0(uint64_t* p, int64_t words) {
-    if (words <= 0) return;
-    before("memset");
-    if (!dry) check(cudaMemsetAsync(p, 0, (size_t)words * 8, s), "cudaMemsetAsync");
-    launched("memset");
-  }
-  // Copy a host blob to a fresh workspace region through the pinned stage.
-  void* upload(const std::vector<char>& blob) {
-    void* d = alloc(blob.size());
-    if (dry || blob.empty()) return d;
-    if (ctx->stage_pending) {
-      check(cudaEventSynchronize(ctx->stage_done), "cudaEventSynchronize");
-      ctx->stage_pending = false;
-    }
-    if (ctx->h_stage_size < blob.size()) {
-      if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-      ctx->h_stage = nullptr;
-      ctx->h_stage_size = 0;
-      size_t sz = std::max<size_t>(blob.size(), 1 << 16);
-      check(cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage), sz), "cudaMallocHost");
-      ctx->h_stage_size = sz;
-    }
-    memcpy(ctx->h_stage, blob.data(), blob.size());
-    check(cudaMemcpyAsync(d, ctx->h_stage, blob.size(), cudaMemcpyHostToDevice, s),
-          "cudaMemcpyAsync");
-    check(cudaEventRecord(ctx->stage_done, s), "cudaEventRecord");
-    ctx->stage_pending = true;
-    return d;
-  }
+  void fail(pa_status st, const std::string& msg) { throw Fail{set_err(ctx, st, msg)}; }
 };
-
-template <class T>
-size_t blob_put(std::vector<char>& blob, const T* data, size_t n) {
-  size_t off = (blob.size() + 15) / 16 * 16;
-  blob.resize(off + sizeof(T) * n);
-  if (n) memcpy(blob.data() + off, data, sizeof(T) * n);
-  return off;
-}
 
 // ------------------------------------------------------------ bit arrays
 BitArr from_pa(const pa_array& a) {
@@ -176,7 +161,7 @@ bool same_layout(const BitArr& x, const BitArr& y) {
 
 // out <- in with axes matched by variable; input axes missing from out are
 // OR-reduced, output axes missing from in are broadcast.
-void reshape(Exec& ex, const BitArr& in, const BitArr& out) {
+void reshape(Builder& bd, const BitArr& in, const BitArr& out) {
   ReshapeDesc d;
   memset(&d, 0, sizeof d);
   d.in = in.w;
@@ -218,21 +203,22 @@ void reshape(Exec& ex, const BitArr& in, const BitArr& out) {
   }
   for (int q = 0; wm && q < d.nred; ++q) wm = (d.red_col_stride[q] == 0);
   d.word_mode = wm ? 1 : 0;
-  ex.st.n_reshapes++;
-  ex.before("reshape_kernel");
-  if (!ex.dry) launch_reshape(d, ex.s);
-  ex.launched("reshape_kernel");
+  bd.st.n_reshapes++;
+  Op op;
+  op.kind = OP_RESHAPE;
+  op.rd = d;
+  bd.ops.push_back(op);
 }
 
 // Bring `x` into layout `want` (vars/res/inner of want; want.w ignored).  Returns
 // x itself when the layouts already agree.
-BitArr conform(Exec& ex, const BitArr& x, BitArr want) {
+BitArr conform(Builder& bd, const BitArr& x, BitArr want) {
   if (same_layout(x, want)) {
     want.w = x.w;
     return want;
   }
-  want.w = ex.alloc_words(want.words());
-  reshape(ex, x, want);
+  want.w = bd.alloc_words(want.words());
+  reshape(bd, x, want);
   return want;
 }
 
@@ -247,37 +233,47 @@ BitArr make_arr(const std::vector<int>& vars, const std::vector<int64_t>& vres, 
   return a;
 }
 
-bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
-
-// One two-array cluster (Eq. GAM on X and Y, outer pack `keep`).  When `target`
-// is given (non-null words) and the result lands in its layout, the result is
-// written there directly.
-// Contractions prepared by join() and launched together by flush_rowor().
-struct PendingRowOr {
-  std::vector<RowOrDesc> d;
-};
-
-void flush_rowor(Exec& ex, PendingRowOr& pend) {
-  // one launch per tile width, at most kRowOrMaxBatch contractions each
-  std::vector<int> done(pend.d.size(), 0);
-  for (size_t i = 0; i < pend.d.size(); ++i) {
+// The waiting contractions as launches: one per tile width.
+void flush_rowor(Builder& bd) {
+  std::vector<int> done(bd.pend.size(), 0);
+  for (size_t i = 0; i < bd.pend.size(); ++i) {
     if (done[i]) continue;
     std::vector<RowOrDesc> group;
-    for (size_t j = i; j < pend.d.size() && (int)group.size() < kRowOrMaxBatch; ++j)
-      if (!done[j] && pend.d[j].Nt == pend.d[i].Nt) {
-        group.push_back(pend.d[j]);
+    for (size_t j = i; j < bd.pend.size(); ++j)
+      if (!done[j] && bd.pend[j].Nt == bd.pend[i].Nt) {
+        group.push_back(bd.pend[j]);
         done[j] = 1;
       }
-    ex.before("rowor_kernel");
-    if (!ex.dry) ex.check(launch_rowor(group.data(), (int)group.size(), ex.s), "rowor_kernel");
-    ex.launched("rowor_kernel");
+    std::vector<CUtensorMap> maps(group.size());
+    std::vector<int64_t> cta0(group.size() + 1, 0);
+    size_t smem = 0;
+    for (size_t p = 0; p < group.size(); ++p) {
+      if (bd.dry) memset(&maps[p], 0, sizeof(CUtensorMap));
+      else if (rowor_encode_map(group[p], &maps[p]) != cudaSuccess)
+        bd.fail(PA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      cta0[p + 1] = cta0[p] + rowor_ctas(group[p]);
+      smem = std::max(smem, rowor_smem_bytes(group[p]));
+    }
+    Op op;
+    op.kind = OP_ROWOR;
+    op.off0 = bd.put(group.data(), group.size(), 64);
+    op.off1 = bd.put(maps.data(), maps.size(), 128);
+    op.off2 = bd.put(cta0.data(), cta0.size(), 16);
+    op.n = (int)group.size();
+    op.count = cta0.back();
+    op.smem = smem;
+    op.i0 = group[0].Nt;
+    if (op.count > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "contraction grid too large");
+    bd.ops.push_back(op);
   }
-  pend.d.clear();
+  bd.pend.clear();
 }
 
-BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
-            const std::vector<int64_t>& vres, const BitArr* target,
-            PendingRowOr* pend = nullptr, int64_t target_ctas = 152) {
+// One two-array cluster (Eq. GAM on X and Y, outer pack `keep`).  When `target`
+// is given and the result lands in its layout, the result is written there.
+// Row-OR contractions wait in bd.pend for flush_rowor.
+BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
+            const std::vector<int64_t>& vres, const BitArr* target, int64_t target_ctas) {
   std::vector<int> xv(X.vars, X.vars + X.ndim), yv(Y.vars, Y.vars + Y.ndim);
   double cost = 1.0;
   {
@@ -286,8 +282,8 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
       if (!has(u, v)) u.push_back(v);
     for (int v : u) cost *= (double)vres[v];
   }
-  ex.st.pixel_ops_dense += cost;
-  ex.st.n_joins++;
+  bd.st.pixel_ops_dense += cost;
+  bd.st.n_joins++;
 
   auto classify = [&](const std::vector<int>& av, const std::vector<int>& bv,
                       std::vector<int>& batch, std::vector<int>& M, std::vector<int>& K,
@@ -312,13 +308,18 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
     bool use_target = target && target->w && target->ndim == (int)keep.size();
     for (int i = 0; use_target && i < target->ndim; ++i) use_target = has(keep, target->vars[i]);
     BitArr want = use_target ? *target : make_arr(keep, vres, keep.empty() ? 0 : 1);
-    BitArr xa = conform(ex, X, make_arr(std::vector<int>(want.vars, want.vars + want.ndim), vres, want.inner));
-    BitArr ya = conform(ex, Y, make_arr(std::vector<int>(want.vars, want.vars + want.ndim), vres, want.inner));
+    std::vector<int> wv(want.vars, want.vars + want.ndim);
+    BitArr xa = conform(bd, X, make_arr(wv, vres, want.inner));
+    BitArr ya = conform(bd, Y, make_arr(wv, vres, want.inner));
     BitArr out = want;
-    if (!out.w) out.w = ex.alloc_words(out.words());
-    ex.before("and_kernel");
-    if (!ex.dry) launch_and(xa.w, ya.w, out.w, out.words(), ex.s);
-    ex.launched("and_kernel");
+    if (!out.w) out.w = bd.alloc_words(out.words());
+    Op op;
+    op.kind = OP_AND;
+    op.a = xa.w;
+    op.b = ya.w;
+    op.p = out.w;
+    op.count = out.words();
+    bd.ops.push_back(op);
     return out;
   }
 
@@ -337,18 +338,14 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
     const BitArr& B = swap ? X : Y;
     std::vector<int> av(A.vars, A.vars + A.ndim), bv(B.vars, B.vars + B.ndim);
     classify(av, bv, c.batch, c.M, c.K, c.N);
-    std::vector<int> a_axes = c.batch, b_axes = c.batch, c_axes = c.batch;
+    std::vector<int> a_axes = c.batch, b_axes = c.batch;
     a_axes.insert(a_axes.end(), c.M.begin(), c.M.end());
     a_axes.insert(a_axes.end(), c.K.begin(), c.K.end());
     b_axes.insert(b_axes.end(), c.K.begin(), c.K.end());
     b_axes.insert(b_axes.end(), c.N.begin(), c.N.end());
-    c_axes.insert(c_axes.end(), c.M.begin(), c.M.end());
-    c_axes.insert(c_axes.end(), c.N.begin(), c.N.end());
     c.reshape_bits = 0;
-    BitArr wa = make_arr(a_axes, vres, (int)c.K.size());
-    BitArr wb = make_arr(b_axes, vres, (int)c.N.size());
-    if (!same_layout(A, wa)) c.reshape_bits += (double)A.bits();
-    if (!same_layout(B, wb)) c.reshape_bits += (double)B.bits();
+    if (!same_layout(A, make_arr(a_axes, vres, (int)c.K.size()))) c.reshape_bits += (double)A.bits();
+    if (!same_layout(B, make_arr(b_axes, vres, (int)c.N.size()))) c.reshape_bits += (double)B.bits();
     double nb = 1;
     for (int v : c.N) nb *= (double)vres[v];
     c.nbits = nb;
@@ -366,11 +363,11 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
   b_axes.insert(b_axes.end(), ch.N.begin(), ch.N.end());
   c_axes.insert(c_axes.end(), ch.M.begin(), ch.M.end());
   c_axes.insert(c_axes.end(), ch.N.begin(), ch.N.end());
-  BitArr Am = conform(ex, A, make_arr(a_axes, vres, (int)ch.K.size()));
-  BitArr Bm = conform(ex, B, make_arr(b_axes, vres, (int)ch.N.size()));
+  BitArr Am = conform(bd, A, make_arr(a_axes, vres, (int)ch.K.size()));
+  BitArr Bm = conform(bd, B, make_arr(b_axes, vres, (int)ch.N.size()));
   BitArr C = make_arr(c_axes, vres, (int)ch.N.size());
   if (target && target->w && same_layout(C, *target)) C.w = target->w;
-  else C.w = ex.alloc_words(C.words());
+  else C.w = bd.alloc_words(C.words());
 
   RowOrDesc d;
   memset(&d, 0, sizeof d);
@@ -385,18 +382,20 @@ BitArr join(Exec& ex, const BitArr& X, const BitArr& Y, const std::vector<int>& 
   for (int v : ch.K) d.K *= vres[v];
   d.Nw = Bm.row_words();
   d.a_row_words = Am.row_words();
-  d.err = ex.ctx->d_err;
-  d.stat = ex.ctx->prof ? ex.ctx->d_stat : nullptr;
+  d.err = bd.d_err;
+  d.stat = bd.d_stat;
+  if (d.M > 0x7fffffffLL || d.K > 0x7fffffffLL)
+    bd.fail(PA_ERR_TOO_LARGE, "contraction with more than 2^31 rows");
   rowor_plan(d, target_ctas);
-  if (d.atomic) ex.memset0(C.w, C.words());
-  if (pend) {
-    pend->d.push_back(d);
-  } else {
-    PendingRowOr one;
-    one.d.push_back(d);
-    flush_rowor(ex, one);
+  if (d.atomic) {
+    Op op;
+    op.kind = OP_MEMSET;
+    op.p = C.w;
+    op.count = C.words();
+    bd.ops.push_back(op);
   }
-  ex.st.peak_words = std::max<int64_t>(ex.st.peak_words, C.words());
+  bd.pend.push_back(d);
+  bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
   return C;
 }
 
@@ -454,20 +453,26 @@ void check_array(pa_ctx* ctx, const pa_array* a, const char* name) {
 }
 
 // ------------------------------------------------------------ plotting
-// Plot all relations into fresh workspace arrays (or into `direct_out`, when
-// given, for a single relation): one preparation launch (row polynomials,
-// thresholds, FP32 centre tables) and one plot launch for all of them.
-std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32_t nrel,
-                             const pa_relation* rels, int strict, const BitArr* direct_out) {
-  (void)nvars;
+// One relation to plot: the relation, the axes of its system, where to put it.
+struct PlotReq {
+  const pa_relation* rel;
+  const pa_axis* axes;
+  int strict;
+  uint64_t* direct;  // plot straight into this array (pa_plot), else workspace
+};
+
+// Every requested plot in one preparation launch (row polynomials, thresholds,
+// FP32 centre tables) and one plot launch.
+std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
+  const int nrel = (int)reqs.size();
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
-  std::vector<char> blob;
   std::vector<size_t> coeff_off(nrel);
   int64_t tiles = 0, prep_items = 0;
-  int max_rows = 1, max_deg = 0, common_deg = rels[0].degree, max_res_last = 1;
+  int max_rows = 1, max_deg = 0, common_deg = reqs[0].rel->degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
-    const pa_relation& r = rels[i];
+    const pa_relation& r = *reqs[i].rel;
+    const pa_axis* axes = reqs[i].axes;
     std::vector<int> dv = distinct_vars(r);
     BitArr a;
     a.ndim = (int)dv.size();
@@ -476,13 +481,13 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
       a.vars[k] = dv[k];
       a.res[k] = axes[dv[k]].res;
     }
-    a.w = direct_out ? direct_out->w : ex.alloc_words(a.words());
+    a.w = reqs[i].direct ? reqs[i].direct : bd.alloc_words(a.words());
     plots.push_back(a);
     // coefficients in nest order
     std::vector<int64_t> ord = nest_order(r.arity, r.degree);
     std::vector<double> nc(ord.size());
     for (size_t k = 0; k < ord.size(); ++k) nc[k] = r.coeffs[ord[k]];
-    coeff_off[i] = blob_put(blob, nc.data(), nc.size());
+    coeff_off[i] = bd.put(nc.data(), nc.size());
 
     PlotJob& J = jobs[i];
     memset(&J, 0, sizeof J);
@@ -490,7 +495,7 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
     J.arity = r.arity;
     J.degree = r.degree;
     J.kind = r.kind;
-    J.strict = strict;
+    J.strict = reqs[i].strict;
     J.ndim = a.ndim;
     for (int k = 0; k < a.ndim; ++k) J.res[k] = (int32_t)a.res[k];
     for (int p = 0; p < r.arity; ++p) {
@@ -505,10 +510,10 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
     const int64_t res_last = a.res[a.ndim - 1];
     const int D1 = r.degree + 1;
     if (J.hoisted) {
-      J.g64 = static_cast<double*>(ex.alloc((size_t)J.nrows * D1 * 8));
-      J.g32 = static_cast<float*>(ex.alloc((size_t)J.nrows * D1 * 4));
-      J.thr = static_cast<float*>(ex.alloc((size_t)J.nrows * 2 * 4));
-      J.y32 = static_cast<float*>(ex.alloc((size_t)res_last * 4));
+      J.g64 = static_cast<double*>(bd.alloc((size_t)J.nrows * D1 * 8));
+      J.g32 = static_cast<float*>(bd.alloc((size_t)J.nrows * D1 * 4));
+      J.thr = static_cast<float*>(bd.alloc((size_t)J.nrows * 2 * 4));
+      J.y32 = static_cast<float*>(bd.alloc((size_t)res_last * 4));
       J.prep0 = prep_items;
       prep_items += J.nrows + res_last;
     }
@@ -540,42 +545,40 @@ std::vector<BitArr> plot_all(Exec& ex, int32_t nvars, const pa_axis* axes, int32
       J.eps32 = 0.0f;
       J.kfac = INFINITY;
     }
-    ex.st.pixels_plotted += (double)a.bits();
-    ex.st.n_plots++;
+    bd.st.pixels_plotted += (double)a.bits();
+    bd.st.n_plots++;
   }
   // prep items are assigned to jobs by binary search on prep0: give the jobs
   // without preparation work the offset of the next one so the search skips them
   for (int i = nrel - 1; i >= 0; --i)
     if (!jobs[i].hoisted) jobs[i].prep0 = (i + 1 < nrel) ? jobs[i + 1].prep0 : prep_items;
-  if (tiles > 0x7fffffffLL) throw Fail{set_err(ex.ctx, PA_ERR_TOO_LARGE, "plot grid too large")};
-  const size_t jobs_off = blob_put(blob, jobs.data(), jobs.size());
-  char* dblob = nullptr;
-  if (ex.dry) {
-    dblob = static_cast<char*>(ex.alloc(blob.size()));
-  } else {
-    // patch device coefficient pointers, then upload
-    // (the device address of the blob is known only after allocation)
-    const size_t off = (ex.used + kAlign - 1) / kAlign * kAlign;
-    char* base = ex.ctx->arena + off;
-    PlotJob* hj = reinterpret_cast<PlotJob*>(blob.data() + jobs_off);
-    for (int i = 0; i < nrel; ++i)
-      hj[i].coeffs = reinterpret_cast<const double*>(base + coeff_off[i]);
-    dblob = static_cast<char*>(ex.upload(blob));
-  }
-  const PlotJob* djobs = reinterpret_cast<const PlotJob*>(dblob + jobs_off);
+  if (tiles > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "plot grid too large");
+  for (int i = 0; i < nrel; ++i)
+    jobs[i].coeffs = reinterpret_cast<const double*>(bd.dev(coeff_off[i]));
+  const size_t jobs_off = bd.put(jobs.data(), jobs.size(), 64);
   if (prep_items > 0) {
-    ex.before("plot_prep_kernel");
-    if (!ex.dry) launch_plot_prep(djobs, nrel, prep_items, ex.s);
-    ex.launched("plot_prep_kernel");
+    Op op;
+    op.kind = OP_PREP;
+    op.off0 = jobs_off;
+    op.n = nrel;
+    op.count = prep_items;
+    bd.ops.push_back(op);
   }
-  ex.before("plot_kernel");
-  if (!ex.dry) launch_plot(djobs, nrel, tiles, max_rows, max_deg, common_deg, max_res_last, ex.s);
-  ex.launched("plot_kernel");
+  Op op;
+  op.kind = OP_PLOT;
+  op.off0 = jobs_off;
+  op.n = nrel;
+  op.count = tiles;
+  op.i0 = max_rows;
+  op.i1 = max_deg;
+  op.i2 = common_deg;
+  op.i3 = max_res_last;
+  bd.ops.push_back(op);
   return plots;
 }
 
-// --------------------------------------------------------- solve (one pass)
-struct SolveArgs {
+// ------------------------------------------------------- networks
+struct Network {
   int32_t nvars;
   const pa_axis* axes;
   int32_t nrel;
@@ -584,49 +587,131 @@ struct SolveArgs {
   int strict;
   int order;
   const int32_t* pairs;
-  const pa_array* out;
+  BitArr target;
 };
 
-void solve_pass(Exec& ex, const SolveArgs& a) {
-  std::vector<int64_t> vres(a.nvars);
-  std::vector<double> vresd(a.nvars);
-  for (int v = 0; v < a.nvars; ++v) {
-    vres[v] = a.axes[v].res;
-    vresd[v] = a.axes[v].res;
-  }
-  std::vector<std::vector<int>> rv;
-  for (int i = 0; i < a.nrel; ++i) rv.push_back(distinct_vars(a.rels[i]));
-  Plan plan = plan_joins(a.nvars, vresd, rv, a.exposed, a.order, a.pairs);
-  BitArr target = from_pa(*a.out);
+// Plots of all networks in one launch pair, then their joins level by level:
+// the joins of one level of every network's cluster tree are independent and
+// share one contraction launch per tile width.
+void build_networks(Builder& bd, std::vector<Network>& nets) {
+  std::vector<PlotReq> reqs;
+  for (auto& n : nets)
+    for (int i = 0; i < n.nrel; ++i) reqs.push_back({&n.rels[i], n.axes, n.strict, nullptr});
+  std::vector<BitArr> plots = plot_all(bd, reqs);
 
-  std::vector<BitArr> slots = plot_all(ex, a.nvars, a.axes, a.nrel, a.rels, a.strict, nullptr);
-  // Joins whose inputs are ready at the same time (same depth in the cluster
-  // tree) are independent: their contractions share one launch.
-  const int nj = (int)plan.joins.size();
-  std::vector<int> level(a.nrel + nj, 0);
+  struct State {
+    Plan plan;
+    std::vector<int64_t> vres;
+    std::vector<BitArr> slots;
+    std::vector<int> level;
+  };
+  std::vector<State> S(nets.size());
   int max_level = 0;
-  for (int t = 0; t < nj; ++t) {
-    const Join& jn = plan.joins[t];
-    level[a.nrel + t] = 1 + std::max(level[jn.a], level[jn.b]);
-    max_level = std::max(max_level, level[a.nrel + t]);
+  size_t pidx = 0;
+  for (size_t k = 0; k < nets.size(); ++k) {
+    Network& n = nets[k];
+    State& s = S[k];
+    s.vres.resize(n.nvars);
+    std::vector<double> vresd(n.nvars);
+    for (int v = 0; v < n.nvars; ++v) {
+      s.vres[v] = n.axes[v].res;
+      vresd[v] = n.axes[v].res;
+    }
+    std::vector<std::vector<int>> rv;
+    for (int i = 0; i < n.nrel; ++i) rv.push_back(distinct_vars(n.rels[i]));
+    s.plan = plan_joins(n.nvars, vresd, rv, n.exposed, n.order, n.pairs);
+    for (int i = 0; i < n.nrel; ++i) s.slots.push_back(plots[pidx++]);
+    const int nj = (int)s.plan.joins.size();
+    s.slots.resize(n.nrel + nj);
+    s.level.assign(n.nrel + nj, 0);
+    for (int t = 0; t < nj; ++t) {
+      const Join& jn = s.plan.joins[t];
+      s.level[n.nrel + t] = 1 + std::max(s.level[jn.a], s.level[jn.b]);
+      max_level = std::max(max_level, s.level[n.nrel + t]);
+    }
   }
-  slots.resize(a.nrel + nj);
-  PendingRowOr pend;
   for (int lv = 1; lv <= max_level; ++lv) {
     int n_in_level = 0;
-    for (int t = 0; t < nj; ++t) n_in_level += (level[a.nrel + t] == lv);
+    for (size_t k = 0; k < nets.size(); ++k)
+      for (size_t t = 0; t < S[k].plan.joins.size(); ++t)
+        n_in_level += (S[k].level[nets[k].nrel + t] == lv);
     const int64_t target_ctas = std::max<int64_t>(1, 152 / std::max(1, n_in_level));
-    for (int t = 0; t < nj; ++t) {
-      if (level[a.nrel + t] != lv) continue;
-      const Join& jn = plan.joins[t];
-      const bool last = (t + 1 == nj);
-      slots[a.nrel + t] = join(ex, slots[jn.a], slots[jn.b], jn.keep, vres,
-                               last ? &target : nullptr, &pend, target_ctas);
+    for (size_t k = 0; k < nets.size(); ++k) {
+      State& s = S[k];
+      const int nrel = nets[k].nrel, nj = (int)s.plan.joins.size();
+      for (int t = 0; t < nj; ++t) {
+        if (s.level[nrel + t] != lv) continue;
+        const Join& jn = s.plan.joins[t];
+        const bool last = (t + 1 == nj);
+        s.slots[nrel + t] = join(bd, s.slots[jn.a], s.slots[jn.b], jn.keep, s.vres,
+                                 last ? &nets[k].target : nullptr, target_ctas);
+      }
     }
-    flush_rowor(ex, pend);
+    flush_rowor(bd);
   }
-  const BitArr& root = slots[plan.root];
-  if (root.w != target.w) reshape(ex, root, target);
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const BitArr& root = S[k].slots[S[k].plan.root];
+    if (root.w != nets[k].target.w) reshape(bd, root, nets[k].target);
+  }
+}
+
+// ------------------------------------------------------------ running
+cudaEvent_t next_event(pa_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) throw Fail{set_err(ctx, PA_ERR_CUDA, "cudaEventCreate")};
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+
+void check_cuda(pa_ctx* ctx, cudaError_t e, const char* what) {
+  if (e != cudaSuccess)
+    throw Fail{set_err(ctx, PA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e))};
+}
+
+// Launch the ops of a program whose blob lives at device address `blob`.
+void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s, bool timing) {
+  for (const Op& op : ops) {
+    pa_ctx::Rec rec;
+    if (timing) {
+      rec.name = op_name(op);
+      rec.a = next_event(ctx);
+      rec.b = next_event(ctx);
+      check_cuda(ctx, cudaEventRecord(rec.a, s), "cudaEventRecord");
+    }
+    switch (op.kind) {
+      case OP_PREP:
+        launch_plot_prep(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, s);
+        break;
+      case OP_PLOT:
+        launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
+                    op.i1, op.i2, op.i3, s);
+        break;
+      case OP_MEMSET:
+        check_cuda(ctx, cudaMemsetAsync(op.p, 0, (size_t)op.count * 8, s), "cudaMemsetAsync");
+        break;
+      case OP_RESHAPE:
+        launch_reshape(op.rd, s);
+        break;
+      case OP_AND:
+        launch_and(op.a, op.b, op.p, op.count, s);
+        break;
+      case OP_ROWOR:
+        check_cuda(ctx,
+                   launch_rowor(reinterpret_cast<const RowOrDesc*>(blob + op.off0),
+                                reinterpret_cast<const CUtensorMap*>(blob + op.off1),
+                                reinterpret_cast<const int64_t*>(blob + op.off2), op.n, op.count,
+                                op.smem, op.i0, s),
+                   "rowor_kernel");
+        break;
+    }
+    check_cuda(ctx, cudaGetLastError(), op_name(op));
+    if (timing) {
+      check_cuda(ctx, cudaEventRecord(rec.b, s), "cudaEventRecord");
+      ctx->recs.push_back(rec);
+    }
+  }
 }
 
 pa_status ensure_arena(pa_ctx* ctx, size_t need) {
@@ -656,31 +741,113 @@ pa_status ensure_arena(pa_ctx* ctx, size_t need) {
   return PA_OK;
 }
 
+// Copy the blob into the arena through the pinned stage, on the stream.
+void upload_blob(pa_ctx* ctx, const std::vector<char>& blob, cudaStream_t s) {
+  if (blob.empty()) return;
+  if (ctx->stage_pending) {
+    check_cuda(ctx, cudaEventSynchronize(ctx->stage_done), "cudaEventSynchronize");
+    ctx->stage_pending = false;
+  }
+  if (ctx->h_stage_size < blob.size()) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_size = 0;
+    const size_t sz = std::max<size_t>(blob.size() * 2, 1 << 16);
+    check_cuda(ctx, cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage), sz), "cudaMallocHost");
+    ctx->h_stage_size = sz;
+  }
+  memcpy(ctx->h_stage, blob.data(), blob.size());
+  check_cuda(ctx, cudaMemcpyAsync(ctx->arena, ctx->h_stage, blob.size(), cudaMemcpyHostToDevice, s),
+             "cudaMemcpyAsync");
+  check_cuda(ctx, cudaEventRecord(ctx->stage_done, s), "cudaEventRecord");
+  ctx->stage_pending = true;
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Size, build and run one call on the context's arena.
 template <class F>
-pa_status run_two_pass(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body) {
+pa_status run_call(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body) {
   try {
     if (cudaSetDevice(ctx->device) != cudaSuccess) {
       cudaGetLastError();
       return set_err(ctx, PA_ERR_CUDA, "cudaSetDevice failed");
     }
-    Exec dry(ctx, s, true);
+    Builder dry(ctx, true, nullptr, 0);
     body(dry);
-    pa_status st = ensure_arena(ctx, dry.used);
+    const size_t blob_cap = round_up(dry.blob.size() + 64, kAlign);
+    const size_t need = dry.used + blob_cap + kAlign;
+    pa_status st = ensure_arena(ctx, need);
     if (st != PA_OK) return st;
-    Exec ex(ctx, s, false);
-    body(ex);
-    ex.st.workspace_bytes = (int64_t)ex.used;
-    if (stats) *stats = ex.st;
+    Builder bd(ctx, false, ctx->arena, blob_cap);
+    bd.d_err = ctx->d_err;
+    bd.d_stat = ctx->prof ? ctx->d_stat : nullptr;
+    body(bd);
+    if (bd.blob.size() > blob_cap) return set_err(ctx, PA_ERR_CUDA, "internal: blob grew");
+    upload_blob(ctx, bd.blob, s);
+    run_ops(ctx, bd.ops, ctx->arena, s, ctx->prof);
+    bd.st.workspace_bytes = (int64_t)bd.used;
+    bd.st.n_launches = (int32_t)bd.ops.size();
+    if (stats) *stats = bd.st;
     return PA_OK;
   } catch (const Fail& f) {
     return f.st;
   }
 }
 
+// Validate one network and turn it into a Network record.
+void check_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,
+                   const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
+                   const pa_options* opts, pa_array* out, Network& n) {
+  check_axes(ctx, nvars, axes);
+  PA_CHECK_ARG(nrel >= 1 && rels, "at least one relation");
+  for (int i = 0; i < nrel; ++i) check_relation(ctx, rels[i], nvars);
+  PA_CHECK_ARG(nexposed >= 0 && nexposed <= PA_MAX_DIM && (nexposed == 0 || exposed),
+               "exposed: 0..8 variables");
+  check_array(ctx, out, "out");
+  PA_CHECK_ARG(out->ndim == nexposed, "out: ndim must equal nexposed");
+  n.exposed.clear();
+  for (int i = 0; i < nexposed; ++i) {
+    PA_CHECK_ARG(exposed[i] >= 0 && exposed[i] < nvars, "exposed: variable out of range");
+    for (int j = 0; j < i; ++j) PA_CHECK_ARG(exposed[j] != exposed[i], "exposed: repeated");
+    PA_CHECK_ARG(out->vars[i] == exposed[i] && out->res[i] == axes[exposed[i]].res,
+                 "out: vars/res must match the exposed variables");
+    n.exposed.push_back(exposed[i]);
+  }
+  n.order = opts ? opts->order : PA_ORDER_GREEDY;
+  PA_CHECK_ARG(n.order == PA_ORDER_GREEDY || n.order == PA_ORDER_GIVEN || n.order == PA_ORDER_LEFT,
+               "opts: unknown order");
+  n.pairs = nullptr;
+  if (n.order == PA_ORDER_GIVEN) {
+    PA_CHECK_ARG(plan_valid_given(nrel, opts->npairs, opts->pairs),
+                 "opts: pairs must be nrel-1 joins of distinct live slots");
+    n.pairs = opts->pairs;
+  }
+  n.strict = (opts && opts->strict) ? 1 : 0;
+  n.nvars = nvars;
+  n.axes = axes;
+  n.nrel = nrel;
+  n.rels = rels;
+  n.target = from_pa(*out);
+}
+
 }  // namespace
 }  // namespace pa
 
 using namespace pa;
+
+// ---------------------------------------------------------------- batches
+struct pa_batch {
+  pa_ctx* ctx = nullptr;
+  char* mem = nullptr;      // the batch's own workspace; its blob sits at offset 0
+  size_t mem_size = 0;
+  char* h_blob = nullptr;   // pinned host image of the blob, copied in by every replay
+  size_t blob_size = 0;
+  std::vector<Op> ops;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  pa_stats st{};
+};
 
 // ================================================================ C ABI
 extern "C" {
@@ -841,10 +1008,9 @@ pa_status pa_plot(pa_ctx* ctx, const pa_relation* rel, const pa_axis* axes, int3
   } catch (const Fail& f) {
     return f.st;
   }
-  BitArr target = from_pa(*out);
-  return run_two_pass(ctx, static_cast<cudaStream_t>(stream), nullptr, [&](Exec& ex) {
-    plot_all(ex, nvars, axes, 1, rel, strict ? 1 : 0, &target);
-  });
+  PlotReq req{rel, axes, strict ? 1 : 0, out->words};
+  return run_call(ctx, static_cast<cudaStream_t>(stream), nullptr,
+                  [&](Builder& bd) { plot_all(bd, {req}); });
 }
 
 pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t nkeep,
@@ -882,9 +1048,10 @@ pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t
     return f.st;
   }
   BitArr a = from_pa(*A), b = from_pa(*B), target = from_pa(*out);
-  return run_two_pass(ctx, static_cast<cudaStream_t>(stream), nullptr, [&](Exec& ex) {
-    BitArr r = join(ex, a, b, kv, vres, &target);
-    if (r.w != target.w) reshape(ex, r, target);
+  return run_call(ctx, static_cast<cudaStream_t>(stream), nullptr, [&](Builder& bd) {
+    BitArr r = join(bd, a, b, kv, vres, &target, 152);
+    flush_rowor(bd);
+    if (r.w != target.w) reshape(bd, r, target);
   });
 }
 
@@ -893,42 +1060,151 @@ pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int3
                            const pa_options* opts, pa_array* out, pa_stats* stats,
                            void* stream) {
   if (!ctx) return PA_ERR_INVALID_ARG;
-  SolveArgs a;
+  std::vector<Network> nets(1);
   try {
-    check_axes(ctx, nvars, axes);
-    PA_CHECK_ARG(nrel >= 1 && rels, "at least one relation");
-    for (int i = 0; i < nrel; ++i) check_relation(ctx, rels[i], nvars);
-    PA_CHECK_ARG(nexposed >= 0 && nexposed <= PA_MAX_DIM && (nexposed == 0 || exposed),
-                 "exposed: 0..8 variables");
-    check_array(ctx, out, "out");
-    PA_CHECK_ARG(out->ndim == nexposed, "out: ndim must equal nexposed");
-    for (int i = 0; i < nexposed; ++i) {
-      PA_CHECK_ARG(exposed[i] >= 0 && exposed[i] < nvars, "exposed: variable out of range");
-      for (int j = 0; j < i; ++j) PA_CHECK_ARG(exposed[j] != exposed[i], "exposed: repeated");
-      PA_CHECK_ARG(out->vars[i] == exposed[i] && out->res[i] == axes[exposed[i]].res,
-                   "out: vars/res must match the exposed variables");
-      a.exposed.push_back(exposed[i]);
-    }
-    a.order = opts ? opts->order : PA_ORDER_GREEDY;
-    PA_CHECK_ARG(a.order == PA_ORDER_GREEDY || a.order == PA_ORDER_GIVEN || a.order == PA_ORDER_LEFT,
-                 "opts: unknown order");
-    a.pairs = nullptr;
-    if (a.order == PA_ORDER_GIVEN) {
-      PA_CHECK_ARG(plan_valid_given(nrel, opts->npairs, opts->pairs),
-                   "opts: pairs must be nrel-1 joins of distinct live slots");
-      a.pairs = opts->pairs;
-    }
-    a.strict = (opts && opts->strict) ? 1 : 0;
+    check_network(ctx, nvars, axes, nrel, rels, nexposed, exposed, opts, out, nets[0]);
   } catch (const Fail& f) {
     return f.st;
   }
-  a.nvars = nvars;
-  a.axes = axes;
-  a.nrel = nrel;
-  a.rels = rels;
-  a.out = out;
-  return run_two_pass(ctx, static_cast<cudaStream_t>(stream), stats,
-                      [&](Exec& ex) { solve_pass(ex, a); });
+  return run_call(ctx, static_cast<cudaStream_t>(stream), stats,
+                  [&](Builder& bd) { build_networks(bd, nets); });
+}
+
+static pa_status check_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
+                             const pa_options* opts, std::vector<Network>& nets) {
+  try {
+    PA_CHECK_ARG(nsys >= 1 && systems && outs, "batch: null pointer or no systems");
+    PA_CHECK_ARG(!opts || opts->order != PA_ORDER_GIVEN, "batch: given orders are per system");
+    nets.resize(nsys);
+    for (int k = 0; k < nsys; ++k) {
+      const pa_system& s = systems[k];
+      check_network(ctx, s.nvars, s.axes, s.nrel, s.rels, s.nexposed, s.exposed, opts, &outs[k],
+                    nets[k]);
+    }
+    return PA_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+pa_status pa_solve_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
+                         const pa_options* opts, pa_stats* stats, void* stream) {
+  if (!ctx) return PA_ERR_INVALID_ARG;
+  std::vector<Network> nets;
+  pa_status st = check_batch(ctx, nsys, systems, outs, opts, nets);
+  if (st != PA_OK) return st;
+  return run_call(ctx, static_cast<cudaStream_t>(stream), stats,
+                  [&](Builder& bd) { build_networks(bd, nets); });
+}
+
+void pa_batch_destroy(pa_batch* bt);
+
+pa_status pa_batch_create(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
+                          const pa_options* opts, pa_batch** out) {
+  if (!ctx || !out) return PA_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<Network> nets;
+  pa_status st = check_batch(ctx, nsys, systems, outs, opts, nets);
+  if (st != PA_OK) return st;
+  pa_batch* bt = new pa_batch();
+  bt->ctx = ctx;
+  cudaStream_t cs = nullptr;
+  try {
+    check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    Builder dry(ctx, true, nullptr, 0);
+    build_networks(dry, nets);
+    const size_t blob_cap = round_up(dry.blob.size() + 64, kAlign);
+    bt->mem_size = dry.used + blob_cap + kAlign;
+    if (ctx->cap && bt->mem_size > ctx->cap)
+      throw Fail{set_err(ctx, PA_ERR_OOM, "batch workspace exceeds the context's cap")};
+    if (cudaMalloc(reinterpret_cast<void**>(&bt->mem), bt->mem_size) != cudaSuccess) {
+      cudaGetLastError();
+      bt->mem = nullptr;
+      throw Fail{set_err(ctx, PA_ERR_OOM, "cudaMalloc of the batch workspace failed")};
+    }
+    Builder bd(ctx, false, bt->mem, blob_cap);
+    bd.d_err = ctx->d_err;
+    build_networks(bd, nets);
+    bt->ops = bd.ops;
+    bt->st = bd.st;
+    bt->st.workspace_bytes = (int64_t)bd.used;
+    bt->st.n_launches = (int32_t)bd.ops.size();
+    bt->blob_size = bd.blob.size();
+    check_cuda(ctx, cudaMallocHost(reinterpret_cast<void**>(&bt->h_blob),
+                                   std::max<size_t>(1, bt->blob_size)),
+               "cudaMallocHost");
+    memcpy(bt->h_blob, bd.blob.data(), bt->blob_size);
+    // capture the blob copy and every launch as one graph
+    check_cuda(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    check_cuda(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal),
+               "cudaStreamBeginCapture");
+    cudaError_t ce = cudaMemcpyAsync(bt->mem, bt->h_blob, bt->blob_size, cudaMemcpyHostToDevice, cs);
+    bool ran = false;
+    if (ce == cudaSuccess) {
+      try {
+        run_ops(ctx, bt->ops, bt->mem, cs, false);
+        ran = true;
+      } catch (const Fail&) {
+        ran = false;
+      }
+    }
+    cudaError_t ee = cudaStreamEndCapture(cs, &bt->graph);
+    check_cuda(ctx, ce, "cudaMemcpyAsync (capture)");
+    if (!ran) throw Fail{PA_ERR_CUDA};
+    check_cuda(ctx, ee, "cudaStreamEndCapture");
+    check_cuda(ctx, cudaGraphInstantiate(&bt->exec, bt->graph, 0), "cudaGraphInstantiate");
+    cudaStreamDestroy(cs);
+    cs = nullptr;
+    *out = bt;
+    return PA_OK;
+  } catch (const Fail& f) {
+    if (cs) cudaStreamDestroy(cs);
+    pa_batch_destroy(bt);
+    return f.st;
+  }
+}
+
+pa_status pa_batch_run(pa_batch* bt, void* stream) {
+  if (!bt || !bt->exec) return PA_ERR_INVALID_ARG;
+  pa_ctx* ctx = bt->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pa_ctx::Rec rec;
+  try {
+    if (ctx->prof) {
+      rec.name = "batch_graph";
+      rec.a = next_event(ctx);
+      rec.b = next_event(ctx);
+      check_cuda(ctx, cudaEventRecord(rec.a, s), "cudaEventRecord");
+    }
+    check_cuda(ctx, cudaGraphLaunch(bt->exec, s), "cudaGraphLaunch");
+    if (ctx->prof) {
+      check_cuda(ctx, cudaEventRecord(rec.b, s), "cudaEventRecord");
+      ctx->recs.push_back(rec);
+    }
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  return PA_OK;
+}
+
+pa_status pa_batch_stats(const pa_batch* bt, pa_stats* stats) {
+  if (!bt || !stats) return PA_ERR_INVALID_ARG;
+  *stats = bt->st;
+  return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch* bt) {
+  if (!bt) return;
+  if (bt->ctx) cudaSetDevice(bt->ctx->device);
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  if (bt->mem) {
+    cudaDeviceSynchronize();  // replays in flight may still use the workspace
+    cudaFree(bt->mem);
+  }
+  if (bt->h_blob) cudaFreeHost(bt->h_blob);
+  delete bt;
 }
 
 pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const pa_relation* rels,

@@ -125,30 +125,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return false;
 }
 
-struct RowOrMaps {
-  CUtensorMap m[kRowOrMaxBatch];
-};
-struct RowOrBatch {
-  int32_t n;
-  int64_t cta0[kRowOrMaxBatch + 1];
-  RowOrDesc d[kRowOrMaxBatch];
-};
-
+// Launch description: problem p owns CTAs [cta0[p], cta0[p+1]); its
+// descriptor and tensor map (used when d.use_tma) live in global memory.
 template <int G>
 __global__ void __launch_bounds__(kRowOrThreads)
-rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant__ RowOrBatch batch) {
+rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __restrict__ maps,
+                  const int64_t* __restrict__ cta0s, int nprob) {
   extern __shared__ __align__(1024) uint64_t bs[];
+  __shared__ RowOrDesc sd;
+  __shared__ int s_p;
   const int tid = threadIdx.x;
   const int nwarps = blockDim.x >> 5;
-  int p = 0;
-  while (p + 1 < batch.n && batch.cta0[p + 1] <= (int64_t)blockIdx.x) ++p;
-  const RowOrDesc& d = batch.d[p];
-  const CUtensorMap& tmap = maps.m[p];
+  if (tid == 0) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cta0s[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_p = lo;
+    sd = descs[lo];
+  }
+  __syncthreads();
+  const int p = s_p;
+  const RowOrDesc& d = sd;
+  const CUtensorMap* tmap = maps + p;
   const int64_t staged = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
   uint16_t* lists = reinterpret_cast<uint16_t*>(bs + (staged + 1) * G);
   uint64_t* bar = reinterpret_cast<uint64_t*>(lists + (size_t)nwarps * kListCap);
 
-  int64_t cta = (int64_t)blockIdx.x - batch.cta0[p];
+  int64_t cta = (int64_t)blockIdx.x - cta0s[p];
   const int64_t rs = cta % d.row_splits;
   cta /= d.row_splits;
   const int64_t kc = cta % d.k_chunks;
@@ -166,6 +171,8 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the tensor map was written to global memory by a copy before the launch
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
     }
     __syncthreads();
     if (tid == 0) {
@@ -179,7 +186,7 @@ rowor_tile_kernel(const __grid_constant__ RowOrMaps maps, const __grid_constant_
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(bs + (size_t)j * 256 * G)),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
             : "memory");
       }
     }
@@ -351,43 +358,31 @@ size_t rowor_smem_bytes(const RowOrDesc& d) {
 
 int64_t rowor_ctas(const RowOrDesc& d) { return d.nbatch * d.n_tiles * d.k_chunks * d.row_splits; }
 
-cudaError_t launch_rowor(const RowOrDesc* ds, int n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  if (n > kRowOrMaxBatch) return cudaErrorInvalidValue;
-  RowOrMaps maps;
-  RowOrBatch batch;
-  memset(&maps, 0, sizeof maps);
-  memset(&batch, 0, sizeof batch);
-  batch.n = n;
-  size_t smem = 0;
-  const int Nt = ds[0].Nt;
-  for (int p = 0; p < n; ++p) {
-    const RowOrDesc& d = ds[p];
-    if (d.Nt != Nt) return cudaErrorInvalidValue;
-    batch.d[p] = d;
-    batch.cta0[p + 1] = batch.cta0[p] + rowor_ctas(d);
-    smem = std::max(smem, rowor_smem_bytes(d));
-    if (d.use_tma) {
-      const cuuint64_t dims[2] = {(cuuint64_t)d.Nw, (cuuint64_t)(d.nbatch * d.K)};
-      const cuuint64_t strides[1] = {(cuuint64_t)d.Nw * 8};
-      const cuuint32_t box[2] = {(cuuint32_t)d.Nt, 256u};
-      const cuuint32_t estr[2] = {1u, 1u};
-      CUresult r = encode_fn()(&maps.m[p], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
-                               const_cast<uint64_t*>(d.B), dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
-  }
-  const int64_t grid = batch.cta0[n];
-  if (grid <= 0) return cudaSuccess;
+cudaError_t rowor_encode_map(const RowOrDesc& d, CUtensorMap* map) {
+  memset(map, 0, sizeof *map);
+  if (!d.use_tma) return cudaSuccess;
+  const cuuint64_t dims[2] = {(cuuint64_t)d.Nw, (cuuint64_t)(d.nbatch * d.K)};
+  const cuuint64_t strides[1] = {(cuuint64_t)d.Nw * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)d.Nt, 256u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(d.B), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
+                         const int64_t* d_cta0, int nprob, int64_t grid, size_t smem, int Nt,
+                         cudaStream_t s) {
+  if (nprob <= 0 || grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
 #define PA_ROWOR(GG)                                                                         \
   do {                                                                                       \
     cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          (int)smem);                                                         \
-    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(maps, batch);          \
+    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(d_descs, d_maps, d_cta0, \
+                                                                     nprob);                 \
   } while (0)
   switch (Nt) {
     case 1: PA_ROWOR(1); break;

@@ -2,6 +2,7 @@
 // engine.  Nothing here is part of the public C interface (include/pa.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,11 +127,14 @@ struct RowOrDesc {
 // aims at about target_ctas CTAs (several contractions can share one launch).
 void rowor_plan(RowOrDesc& d, int64_t target_ctas);
 size_t rowor_smem_bytes(const RowOrDesc& d);
-constexpr int kRowOrMaxBatch = 16;
-// Independent contractions with the same tile width Nt in one launch
-// (n <= kRowOrMaxBatch).
-cudaError_t launch_rowor(const RowOrDesc* d, int n, cudaStream_t s);
 int64_t rowor_ctas(const RowOrDesc& d);
+// TMA descriptor of d.B (all zero when d.use_tma is 0)
+cudaError_t rowor_encode_map(const RowOrDesc& d, CUtensorMap* map);
+// Independent contractions with the same tile width Nt in one launch:
+// descriptors, tensor maps and CTA offsets (nprob + 1 entries) on the device.
+cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
+                         const int64_t* d_cta0, int nprob, int64_t grid, size_t smem, int Nt,
+                         cudaStream_t s);
 // cudaSuccess when this build holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
