@@ -234,6 +234,35 @@ pa_status pa_batch_run(pa_batch* batch, void* stream);
 pa_status pa_batch_stats(const pa_batch* batch, pa_stats* stats);
 void pa_batch_destroy(pa_batch* batch);
 
+/* pa_solve_network for callers that cannot let the library allocate memory:
+ * code running while a CUDA graph is being captured (cudaMalloc and
+ * cudaMallocHost are not allowed in a capture), real-time loops that cannot
+ * afford the device-wide synchronisation of cudaFree, and hosts whose memory
+ * is budgeted by someone else.  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no pinned host memory, no context.  Its workspace is one static
+ * device array of PA_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which loads
+ * the library holds until the process exits; the inputs and `out` are the
+ * caller's, exactly as for pa_solve_network, and the results are identical.
+ * The paper has no counterpart: this is an engineering variant of Sec. 3.6.
+ *   - Runs on the current CUDA device.  The first call on a device looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call before any stream capture.
+ *   - A system whose workspace would exceed the array returns PA_ERR_TOO_LARGE
+ *     before any launch; stats->workspace_bytes (when stats is not NULL) then
+ *     holds the bytes it would need.
+ *   - Every call shares the array and sees the previous call's contents; each
+ *     call clears what must start at zero.  Calls whose work overlaps on the
+ *     GPU (other streams, other threads) race on the array: order them.
+ *   - Argument errors return PA_ERR_INVALID_ARG; there is no context, so no
+ *     message; a device wait that runs out is not reported by this entry.
+ * The descriptor upload reads pageable host memory and returns once the
+ * driver has copied it. */
+#define PA_STATIC_SCRATCH_BYTES (16u << 20)
+pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes, int32_t nrel,
+                                  const pa_relation* rels, int32_t nexposed,
+                                  const int32_t* exposed, const pa_options* opts, pa_array* out,
+                                  pa_stats* stats, void* stream);
+
 /* The join order pa_solve_network would use (host only, no GPU): writes
  * 2*(nrel-1) slot indices into pairs_out (same numbering as pa_options.pairs). */
 pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const pa_relation* rels,

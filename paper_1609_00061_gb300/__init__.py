@@ -181,6 +181,28 @@ def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pa
     return st.as_dict()
 
 
+def pa_solve_network_static(axes, rels, exposed, out: BitArray, order="greedy", pairs=None,
+                            strict=False, stream=None) -> dict:
+    """pa_solve_network without any allocation by the library: the workspace is a
+    fixed 16 MiB device array (see include/pa.h).  Runs on the current device."""
+    r, keep = _relations(rels)
+    opts = _opts(order, strict)
+    pr = None
+    if pairs is not None:
+        pr = _i32([int(v) for p in pairs for v in p])
+        opts.npairs = len(pairs)
+        opts.pairs = ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32))
+    st = PaStats()
+    o = out.c()
+    status = _lib().pa_solve_network_static(len(axes), _axes(axes), len(rels), r, len(exposed),
+                                            _i32(exposed), ctypes.byref(opts), ctypes.byref(o),
+                                            ctypes.byref(st), _stream_ptr(stream))
+    if status != PA_OK:
+        raise PaError(status, f"static workspace would need {st.workspace_bytes} bytes"
+                      if status == 3 else "")
+    return st.as_dict()
+
+
 def _systems(systems):
     """Marshal workloads.System objects; returns (array, keep-alive list)."""
     arr = (PaSystem * len(systems))()

@@ -111,7 +111,7 @@ EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_word
            "pa_profile_enable", "pa_profile_read",
            "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_solve_batch",
            "pa_batch_create", "pa_batch_run", "pa_batch_stats", "pa_batch_destroy",
-           "pa_plan_order", "pa_tree_cost"]
+           "pa_solve_network_static", "pa_plan_order", "pa_tree_cost"]
 
 _lib = None
 
@@ -161,6 +161,9 @@ def load(build_if_missing: bool = True):
     lib.pa_batch_stats.restype = c_i32
     lib.pa_batch_destroy.argtypes = [vp]
     lib.pa_batch_destroy.restype = None
+    lib.pa_solve_network_static.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32,
+                                            P(c_i32), P(PaOptions), P(PaArray), P(PaStats), vp]
+    lib.pa_solve_network_static.restype = c_i32
     lib.pa_plan_order.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32), c_i32,
                                   P(c_i32), P(c_f64), P(c_i64)]
     lib.pa_plan_order.restype = c_i32

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1248,3 +1249,79 @@ pa_status pa_tree_cost(int32_t nlinks, const double* link_res, int32_t npacks,
 }
 
 }  // extern "C"
+
+// ================================================= solve without allocation
+// pa_solve_network_static: the whole-method solve with its workspace in a
+// fixed device array instead of memory the library allocates.  The array's
+// host-side name is only a stand-in; its device address is looked up once per
+// device (cudaGetSymbolAddress, with that device current) and cached.
+static __device__ __align__(256) unsigned char g_pa_static_scratch[PA_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 256;
+char* g_static_addr[kMaxDevices] = {};
+constexpr size_t kStaticHeader = 256;  // device error word lives here
+}  // namespace
+
+extern "C" pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes, int32_t nrel,
+                                             const pa_relation* rels, int32_t nexposed,
+                                             const int32_t* exposed, const pa_options* opts,
+                                             pa_array* out, pa_stats* stats, void* stream) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return PA_ERR_CUDA;
+  }
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_pa_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PA_ERR_CUDA;
+      }
+      g_static_addr[dev] = static_cast<char*>(p);
+    }
+    base = g_static_addr[dev];
+  }
+  pa_ctx* ctx = nullptr;  // no context: errors are reported by the return code only
+  std::vector<Network> nets(1);
+  try {
+    check_network(ctx, nvars, axes, nrel, rels, nexposed, exposed, opts, out, nets[0]);
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    Builder dry(ctx, true, nullptr, 0);
+    build_networks(dry, nets);
+    const size_t blob_cap = round_up(dry.blob.size() + 64, kAlign);
+    const size_t need = kStaticHeader + dry.used + blob_cap + kAlign;
+    if (need > PA_STATIC_SCRATCH_BYTES) {
+      if (stats) {
+        *stats = dry.st;
+        stats->workspace_bytes = (int64_t)need;
+      }
+      return PA_ERR_TOO_LARGE;
+    }
+    char* work = base + kStaticHeader;
+    Builder bd(ctx, false, work, blob_cap);
+    bd.d_err = reinterpret_cast<int*>(base);
+    build_networks(bd, nets);
+    if (bd.blob.size() > blob_cap) return PA_ERR_CUDA;
+    // the array keeps the previous call's contents: the error word starts at zero
+    check_cuda(ctx, cudaMemsetAsync(base, 0, kStaticHeader, s), "cudaMemsetAsync");
+    // pageable source: the copy returns once the driver has taken the bytes
+    check_cuda(ctx, cudaMemcpyAsync(work, bd.blob.data(), bd.blob.size(), cudaMemcpyHostToDevice, s),
+               "cudaMemcpyAsync");
+    run_ops(ctx, bd.ops, work, s, false);
+    bd.st.workspace_bytes = (int64_t)(kStaticHeader + bd.used);
+    bd.st.n_launches = (int32_t)bd.ops.size() + 2;
+    if (stats) *stats = bd.st;
+    return PA_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
