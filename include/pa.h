@@ -117,8 +117,12 @@ typedef struct {
 typedef enum {
   PA_ORDER_GREEDY = 0, /* repeatedly join the pair with the smallest result */
   PA_ORDER_GIVEN = 1,  /* join the pairs listed in pa_options.pairs */
-  PA_ORDER_LEFT = 2    /* fold the relations left to right */
+  PA_ORDER_LEFT = 2,   /* fold the relations left to right */
+  PA_ORDER_LEARNED = 3 /* rank candidate orders with a learned cost model
+                          (pa_options.model); the greedy order is the fallback */
 } pa_order;
+
+typedef struct pa_mlp pa_mlp;
 
 typedef struct {
   int32_t strict;       /* 1: strict comparison (see above); 0: default */
@@ -126,6 +130,8 @@ typedef struct {
   int32_t npairs;       /* PA_ORDER_GIVEN: nrel - 1 joins */
   const int32_t* pairs; /* PA_ORDER_GIVEN: 2*npairs slot indices, host; slots
                            0..nrel-1 are the plots, join t creates slot nrel+t */
+  const pa_mlp* model;  /* PA_ORDER_LEARNED: the cost model */
+  int32_t ncand;        /* PA_ORDER_LEARNED: candidate orders per system (0: 16) */
 } pa_options;
 
 typedef struct {
@@ -262,6 +268,55 @@ pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes, int32_t nr
                                   const pa_relation* rels, int32_t nexposed,
                                   const int32_t* exposed, const pa_options* opts, pa_array* out,
                                   pa_stats* stats, void* stream);
+
+/* ------------------------------------------------------------ learned order
+ * A small FP32 network (PA_FEATURES inputs, `nlayers` hidden layers of
+ * `hidden` ReLU units, one linear output) predicts log2(microseconds)/8 of a
+ * join from PA_FEATURES numbers the library computes for it: sizes of the
+ * matrix form, the naive cost r^Lambda (Sec. 3.5), estimated operand and
+ * result densities, reshape volume.  Plot densities are estimated on the host
+ * from 512 sampled pixel centres, join densities propagated under an
+ * independence assumption, so planning never waits for the solve.
+ * PA_ORDER_LEARNED ranks `ncand` candidate orders per system (greedy,
+ * smallest-cost, left-to-right and seeded randomised greedy variants) by the
+ * predicted total time; the greedy order is the judge: the learned choice is
+ * kept only when its predicted time is lower and its largest intermediate is
+ * at most 4x the greedy one.  Any order gives the same bits. */
+#define PA_FEATURES 16
+pa_status pa_mlp_create(pa_ctx* ctx, int32_t hidden, int32_t nlayers, uint64_t seed,
+                        pa_mlp** model);
+void pa_mlp_destroy(pa_mlp* model);
+int64_t pa_mlp_num_params(const pa_mlp* model);
+/* Parameters and the last gradient as one flat FP32 vector (host memory):
+ * per layer the weights [out][in] row-major, then the biases. */
+pa_status pa_mlp_get_params(const pa_mlp* model, float* params);
+pa_status pa_mlp_set_params(pa_mlp* model, const float* params);
+pa_status pa_mlp_get_grads(const pa_mlp* model, float* grads);
+/* y[n] = net(x[n][PA_FEATURES]); device pointers, enqueued on `stream`. */
+pa_status pa_mlp_forward(pa_mlp* model, const float* x, int32_t n, float* y, void* stream);
+/* Gradient of 0.5 * mean_n (net(x_n) - t_n)^2 with respect to the parameters
+ * (device x, t); *loss (host, may be NULL) receives the loss after a sync. */
+pa_status pa_mlp_backward(pa_mlp* model, const float* x, const float* t, int32_t n, float* loss,
+                          void* stream);
+/* One Adam step on the last gradient. */
+pa_status pa_mlp_adam(pa_mlp* model, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Solver log for training the cost model: solve one system with one join per
+ * launch, time every join with CUDA events (its reshapes included) and count
+ * the set bits of its result.  Writes, for join t < *njoins (at most
+ * max_joins), features[t*PA_FEATURES ..], micros[t] and densities[t] (the
+ * result's fraction of set bits).  Synchronises the stream. */
+pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts, pa_array* out,
+                      int32_t max_joins, float* features, float* micros, float* densities,
+                      int32_t* njoins, void* stream);
+
+/* The orders PA_ORDER_LEARNED would use, with the judge's inputs: for system k,
+ * pairs_out[offsets..] receives its 2*(nrel_k-1) slot indices (systems packed
+ * one after another), learned[k] whether the learned order was kept, and
+ * pred_us[2k], pred_us[2k+1] the predicted times of the chosen and the greedy
+ * order.  Runs one forward pass on the GPU and waits for it. */
+pa_status pa_plan_learned(pa_ctx* ctx, const pa_mlp* model, int32_t nsys, const pa_system* systems,
+                          int32_t ncand, int32_t* pairs_out, int32_t* learned, float* pred_us);
 
 /* The join order pa_solve_network would use (host only, no GPU): writes
  * 2*(nrel-1) slot indices into pairs_out (same numbering as pa_options.pairs). */

@@ -24,7 +24,8 @@ from ._native import PaArray, PaAxis, PaOptions, PaRelation, PaStats, PaSystem
 PA_OK = 0
 STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
           4: "PA_ERR_OOM", 5: "PA_ERR_CUDA", 6: "PA_ERR_TIMEOUT"}
-ORDERS = {"greedy": 0, "given": 1, "left": 2}
+ORDERS = {"greedy": 0, "given": 1, "left": 2, "learned": 3}
+N_FEATURES = 16
 
 
 class PaError(RuntimeError):
@@ -162,11 +163,9 @@ def pa_contract(ctx, A: BitArray, B: BitArray, keep, out: BitArray, stream=None)
 
 
 def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pairs=None,
-                     strict=False, stream=None) -> dict:
+                     strict=False, stream=None, model=None) -> dict:
     r, keep = _relations(rels)
-    opts = PaOptions()
-    opts.strict = int(bool(strict))
-    opts.order = ORDERS[order] if isinstance(order, str) else int(order)
+    opts = _opts(order, strict, model)
     pr = None
     if pairs is not None:
         flat = [int(v) for p in pairs for v in p]
@@ -221,19 +220,23 @@ def _systems(systems):
     return arr, keep
 
 
-def _opts(order, strict):
+def _opts(order, strict, model=None, ncand=0):
     opts = PaOptions()
     opts.strict = int(bool(strict))
     opts.order = ORDERS[order] if isinstance(order, str) else int(order)
+    opts.model = model.h if model is not None else None
+    opts.ncand = int(ncand)
     return opts
 
 
-def pa_solve_batch(ctx, systems, outs, order="greedy", strict=False, stream=None) -> dict:
+def pa_solve_batch(ctx, systems, outs, order="greedy", strict=False, stream=None, model=None,
+                   ncand=0) -> dict:
     """Solve many independent workloads.System objects in shared launches."""
     arr, keep = _systems(systems)
     oc = (PaArray * len(outs))(*[o.c() for o in outs])
     st = PaStats()
-    _check(_lib().pa_solve_batch(ctx, len(systems), arr, oc, ctypes.byref(_opts(order, strict)),
+    _check(_lib().pa_solve_batch(ctx, len(systems), arr, oc,
+                                 ctypes.byref(_opts(order, strict, model, ncand)),
                                  ctypes.byref(st), _stream_ptr(stream)), ctx)
     return st.as_dict()
 
@@ -241,7 +244,8 @@ def pa_solve_batch(ctx, systems, outs, order="greedy", strict=False, stream=None
 class Batch:
     """A planned batch captured as one CUDA graph (pa_batch_create / pa_batch_run)."""
 
-    def __init__(self, engine, systems, outs=None, order="greedy", strict=False):
+    def __init__(self, engine, systems, outs=None, order="greedy", strict=False, model=None,
+                 ncand=0):
         self.engine = engine
         if outs is None:
             outs = [BitArray.empty(sy.exposed, [sy.axes[v][2] for v in sy.exposed], engine.device)
@@ -251,7 +255,8 @@ class Batch:
         oc = (PaArray * len(outs))(*[o.c() for o in outs])
         h = ctypes.c_void_p()
         _check(_lib().pa_batch_create(engine.ctx, len(systems), arr, oc,
-                                      ctypes.byref(_opts(order, strict)), ctypes.byref(h)),
+                                      ctypes.byref(_opts(order, strict, model, ncand)),
+                                      ctypes.byref(h)),
                engine.ctx)
         self.h = h
 
@@ -361,25 +366,165 @@ class Engine:
         out = BitArray.empty(keep, [res[v] for v in keep], self.device)
         return pa_contract(self.ctx, A, B, keep, out, stream)
 
-    def solve(self, system, order="greedy", pairs=None, strict=False, stream=None, out=None):
+    def solve(self, system, order="greedy", pairs=None, strict=False, stream=None, out=None,
+              model=None):
         """Solve a workloads.System; returns (BitArray over system.exposed, stats)."""
         if out is None:
             out = BitArray.empty(system.exposed, [system.axes[v][2] for v in system.exposed],
                                  self.device)
         st = pa_solve_network(self.ctx, system.axes, system.rels, system.exposed, out, order,
-                              pairs, strict, stream)
+                              pairs, strict, stream, model)
         return out, st
 
-    def solve_batch(self, systems, order="greedy", strict=False, stream=None, outs=None):
+    def solve_batch(self, systems, order="greedy", strict=False, stream=None, outs=None,
+                    model=None, ncand=0):
         """Solve a list of workloads.System; returns (list of BitArray, stats)."""
         if outs is None:
             outs = [BitArray.empty(sy.exposed, [sy.axes[v][2] for v in sy.exposed], self.device)
                     for sy in systems]
-        st = pa_solve_batch(self.ctx, systems, outs, order, strict, stream)
+        st = pa_solve_batch(self.ctx, systems, outs, order, strict, stream, model, ncand)
         return outs, st
 
-    def batch(self, systems, order="greedy", strict=False, outs=None) -> "Batch":
-        return Batch(self, systems, outs, order, strict)
+    def batch(self, systems, order="greedy", strict=False, outs=None, model=None,
+              ncand=0) -> "Batch":
+        return Batch(self, systems, outs, order, strict, model, ncand)
+
+    def log_joins(self, system, order="greedy", pairs=None, model=None, stream=None):
+        """Solve one system with one launch per join; returns (features [n,16],
+        microseconds [n], result densities [n], output BitArray)."""
+        out = BitArray.empty(system.exposed, [system.axes[v][2] for v in system.exposed],
+                             self.device)
+        arr, keep = _systems([system])
+        opts = _opts(order, False, model)
+        pr = None
+        if pairs is not None:
+            pr = _i32([int(v) for p in pairs for v in p])
+            opts.npairs = len(pairs)
+            opts.pairs = ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32))
+        mx = max(1, len(system.rels) - 1)
+        feats = np.zeros((mx, N_FEATURES), dtype=np.float32)
+        us = np.zeros(mx, dtype=np.float32)
+        dens = np.zeros(mx, dtype=np.float32)
+        nj = ctypes.c_int32()
+        o = out.c()
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(_lib().pa_join_log(self.ctx, arr, ctypes.byref(opts), ctypes.byref(o), mx,
+                                  feats.ctypes.data_as(fp), us.ctypes.data_as(fp),
+                                  dens.ctypes.data_as(fp), ctypes.byref(nj), _stream_ptr(stream)),
+               self.ctx)
+        n = nj.value
+        return feats[:n], us[:n], dens[:n], out
+
+    def plan_learned(self, model, systems, ncand=0):
+        """Orders PA_ORDER_LEARNED would pick: (list of pair lists, learned flags,
+        predicted microseconds [n,2] = chosen, greedy)."""
+        arr, keep = _systems(systems)
+        total = sum(2 * (len(sy.rels) - 1) for sy in systems)
+        pairs = (ctypes.c_int32 * max(1, total))()
+        learned = (ctypes.c_int32 * len(systems))()
+        pred = np.zeros(2 * len(systems), dtype=np.float32)
+        _check(_lib().pa_plan_learned(self.ctx, model.h, len(systems), arr, int(ncand), pairs,
+                                      learned, pred.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               self.ctx)
+        out, off = [], 0
+        for sy in systems:
+            n = len(sy.rels) - 1
+            out.append([(pairs[off + 2 * t], pairs[off + 2 * t + 1]) for t in range(n)])
+            off += 2 * n
+        return out, [bool(v) for v in learned], pred.reshape(-1, 2)
 
     def sync(self, stream=None):
         pa_sync(self.ctx, stream)
+
+
+# ------------------------------------------------------------ cost model
+class CostModel:
+    """The learned join-cost model (FP32 MLP; forward, backward and Adam run in
+    the library's own CUDA kernels).  Input: the 16 join features the library
+    computes; output: log2(microseconds) / 8."""
+
+    def __init__(self, engine, hidden=128, nlayers=3, seed=0x160900061):
+        self.engine = engine
+        self.hidden, self.nlayers = hidden, nlayers
+        h = ctypes.c_void_p()
+        _check(_lib().pa_mlp_create(engine.ctx, hidden, nlayers, seed, ctypes.byref(h)), engine.ctx)
+        self.h = h
+
+    @property
+    def n_params(self) -> int:
+        return int(_lib().pa_mlp_num_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(_lib().pa_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(_lib().pa_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_grads(self) -> np.ndarray:
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _check(_lib().pa_mlp_get_grads(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return g
+
+    def forward(self, x, stream=None):
+        """x: CUDA float32 tensor [n, 16] -> CUDA float32 tensor [n]."""
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(_lib().pa_mlp_forward(self.h, ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                     ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream)),
+               self.engine.ctx)
+        return y
+
+    def backward(self, x, t, stream=None) -> float:
+        x, t = x.contiguous(), t.contiguous()
+        loss = ctypes.c_float()
+        _check(_lib().pa_mlp_backward(self.h, ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                      ctypes.byref(loss), _stream_ptr(stream)), self.engine.ctx)
+        return float(loss.value)
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(_lib().pa_mlp_adam(self.h, lr, beta1, beta2, eps, _stream_ptr(stream)),
+               self.engine.ctx)
+
+    def train(self, X, T, epochs=200, batch=256, lr=2e-3, seed=0):
+        """Minibatch Adam on (X [n,16], T [n]) numpy arrays; returns the loss history."""
+        import torch
+        dev = f"cuda:{self.engine.device}"
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+        Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(dev)
+        n = Xd.shape[0]
+        rng = np.random.default_rng(seed)
+        hist = []
+        for ep in range(epochs):
+            perm = torch.from_numpy(rng.permutation(n)).to(dev)
+            tot = 0.0
+            for b0 in range(0, n, batch):
+                idx = perm[b0:b0 + batch]
+                tot += self.backward(Xd[idx], Td[idx]) * idx.numel()
+                self.adam(lr)
+            hist.append(tot / n)
+        return hist
+
+    def save(self, path):
+        np.savez(path, params=self.get_params(), hidden=self.hidden, nlayers=self.nlayers)
+
+    def load(self, path):
+        d = np.load(path)
+        assert int(d["hidden"]) == self.hidden and int(d["nlayers"]) == self.nlayers
+        self.set_params(d["params"])
+
+    def close(self):
+        if self.h:
+            _lib().pa_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

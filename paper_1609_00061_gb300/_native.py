@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
 _ROOT = os.path.dirname(_HERE)
 INCLUDE = os.path.join(_ROOT, "include")
 
-CU_SOURCES = ["api.cu", "plot.cu", "contract.cu"]
+CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu"]
 CPP_SOURCES = ["planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -88,7 +88,7 @@ class PaArray(ctypes.Structure):
 
 class PaOptions(ctypes.Structure):
     _fields_ = [("strict", c_i32), ("order", c_i32), ("npairs", c_i32),
-                ("pairs", ctypes.POINTER(c_i32))]
+                ("pairs", ctypes.POINTER(c_i32)), ("model", ctypes.c_void_p), ("ncand", c_i32)]
 
 
 class PaStats(ctypes.Structure):
@@ -111,7 +111,10 @@ EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_word
            "pa_profile_enable", "pa_profile_read",
            "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_solve_batch",
            "pa_batch_create", "pa_batch_run", "pa_batch_stats", "pa_batch_destroy",
-           "pa_solve_network_static", "pa_plan_order", "pa_tree_cost"]
+           "pa_solve_network_static", "pa_plan_order", "pa_tree_cost",
+           "pa_mlp_create", "pa_mlp_destroy", "pa_mlp_num_params", "pa_mlp_get_params",
+           "pa_mlp_set_params", "pa_mlp_get_grads", "pa_mlp_forward", "pa_mlp_backward",
+           "pa_mlp_adam", "pa_join_log", "pa_plan_learned"]
 
 _lib = None
 
@@ -164,6 +167,27 @@ def load(build_if_missing: bool = True):
     lib.pa_solve_network_static.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32,
                                             P(c_i32), P(PaOptions), P(PaArray), P(PaStats), vp]
     lib.pa_solve_network_static.restype = c_i32
+    fp = P(ctypes.c_float)
+    lib.pa_mlp_create.argtypes = [vp, c_i32, c_i32, ctypes.c_uint64, P(vp)]
+    lib.pa_mlp_create.restype = c_i32
+    lib.pa_mlp_destroy.argtypes = [vp]
+    lib.pa_mlp_destroy.restype = None
+    lib.pa_mlp_num_params.argtypes = [vp]
+    lib.pa_mlp_num_params.restype = c_i64
+    for nm in ("pa_mlp_get_params", "pa_mlp_set_params", "pa_mlp_get_grads"):
+        getattr(lib, nm).argtypes = [vp, fp]
+        getattr(lib, nm).restype = c_i32
+    lib.pa_mlp_forward.argtypes = [vp, vp, c_i32, vp, vp]
+    lib.pa_mlp_forward.restype = c_i32
+    lib.pa_mlp_backward.argtypes = [vp, vp, vp, c_i32, fp, vp]
+    lib.pa_mlp_backward.restype = c_i32
+    lib.pa_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+    lib.pa_mlp_adam.restype = c_i32
+    lib.pa_join_log.argtypes = [vp, P(PaSystem), P(PaOptions), P(PaArray), c_i32, fp, fp, fp,
+                                P(c_i32), vp]
+    lib.pa_join_log.restype = c_i32
+    lib.pa_plan_learned.argtypes = [vp, vp, c_i32, P(PaSystem), c_i32, P(c_i32), P(c_i32), fp]
+    lib.pa_plan_learned.restype = c_i32
     lib.pa_plan_order.argtypes = [c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32), c_i32,
                                   P(c_i32), P(c_f64), P(c_i64)]
     lib.pa_plan_order.restype = c_i32

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "mlp.h"
 #include "pa_internal.h"
 #include "planner.h"
 
@@ -78,6 +79,7 @@ struct Op {
   const uint64_t* a = nullptr;
   const uint64_t* b = nullptr;
   ReshapeDesc rd;
+  int join = -1;                        // join this op belongs to (join logging)
 };
 
 const char* op_name(const Op& op) {
@@ -270,22 +272,34 @@ void flush_rowor(Builder& bd) {
   bd.pend.clear();
 }
 
-// One two-array cluster (Eq. GAM on X and Y, outer pack `keep`).  When `target`
-// is given and the result lands in its layout, the result is written there.
-// Row-OR contractions wait in bd.pend for flush_rowor.
-BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
-            const std::vector<int64_t>& vres, const BitArr* target, int64_t target_ctas) {
+// Shape of one two-array cluster (Eq. GAM on X and Y, outer pack `keep`):
+// either a Hadamard product (nothing summed between X and Y) or a matrix form
+// A[batch][M][K] x B[batch][K][N] -> C[batch][M][N] with A and B chosen so that
+// fewer bits need reshaping, then the wider packed side as B.
+struct JoinShape {
+  bool hadamard = false;
+  bool swap = false;            // A = Y, B = X
+  std::vector<int> a_axes, b_axes, c_axes;
+  int kinner = 0, ninner = 0;   // number of K and N axes
+  int64_t nbatch = 1, M = 1, K = 1;
+  double nbits = 1.0;           // N (bits per output row)
+  double reshape_bits = 0.0;    // bits of operands that need a reshape
+  double cost = 1.0;            // r^Lambda of the cluster (naive cost, Sec. 3.5)
+  double result_bits = 1.0;
+  double private_a = 1.0, private_b = 1.0;  // sizes of the axes reduced away
+};
+
+JoinShape analyze_join(const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
+                       const std::vector<int64_t>& vres) {
+  JoinShape js;
   std::vector<int> xv(X.vars, X.vars + X.ndim), yv(Y.vars, Y.vars + Y.ndim);
-  double cost = 1.0;
   {
     std::vector<int> u = xv;
     for (int v : yv)
       if (!has(u, v)) u.push_back(v);
-    for (int v : u) cost *= (double)vres[v];
+    for (int v : u) js.cost *= (double)vres[v];
   }
-  bd.st.pixel_ops_dense += cost;
-  bd.st.n_joins++;
-
+  for (int v : keep) js.result_bits *= (double)vres[v];
   auto classify = [&](const std::vector<int>& av, const std::vector<int>& bv,
                       std::vector<int>& batch, std::vector<int>& M, std::vector<int>& K,
                       std::vector<int>& N) {
@@ -299,13 +313,80 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     for (int v : bv)
       if (!has(av, v) && has(keep, v)) N.push_back(v);
   };
-
   std::vector<int> batch, M, K, N;
   classify(xv, yv, batch, M, K, N);
-
-  // Hadamard: every kept variable is in both arrays and nothing is summed
-  // between them (only private variables are reduced)
   if (K.empty() && M.empty() && N.empty()) {
+    js.hadamard = true;
+    for (int v : xv)
+      if (!has(keep, v)) js.private_a *= (double)vres[v];
+    for (int v : yv)
+      if (!has(keep, v)) js.private_b *= (double)vres[v];
+    return js;
+  }
+  struct Choice {
+    std::vector<int> batch, M, K, N;
+    double reshape_bits = 0, nbits = 1;
+  };
+  auto evaluate = [&](bool swap) {
+    Choice c;
+    const BitArr& A = swap ? Y : X;
+    const BitArr& B = swap ? X : Y;
+    std::vector<int> av(A.vars, A.vars + A.ndim), bv(B.vars, B.vars + B.ndim);
+    classify(av, bv, c.batch, c.M, c.K, c.N);
+    std::vector<int> a_axes = c.batch, b_axes = c.batch;
+    a_axes.insert(a_axes.end(), c.M.begin(), c.M.end());
+    a_axes.insert(a_axes.end(), c.K.begin(), c.K.end());
+    b_axes.insert(b_axes.end(), c.K.begin(), c.K.end());
+    b_axes.insert(b_axes.end(), c.N.begin(), c.N.end());
+    if (!same_layout(A, make_arr(a_axes, vres, (int)c.K.size()))) c.reshape_bits += (double)A.bits();
+    if (!same_layout(B, make_arr(b_axes, vres, (int)c.N.size()))) c.reshape_bits += (double)B.bits();
+    for (int v : c.N) c.nbits *= (double)vres[v];
+    return c;
+  };
+  Choice c0 = evaluate(false), c1 = evaluate(true);
+  js.swap = (c1.reshape_bits < c0.reshape_bits ||
+             (c1.reshape_bits == c0.reshape_bits && c1.nbits > c0.nbits));
+  const Choice& ch = js.swap ? c1 : c0;
+  js.a_axes = js.b_axes = js.c_axes = ch.batch;
+  js.a_axes.insert(js.a_axes.end(), ch.M.begin(), ch.M.end());
+  js.a_axes.insert(js.a_axes.end(), ch.K.begin(), ch.K.end());
+  js.b_axes.insert(js.b_axes.end(), ch.K.begin(), ch.K.end());
+  js.b_axes.insert(js.b_axes.end(), ch.N.begin(), ch.N.end());
+  js.c_axes.insert(js.c_axes.end(), ch.M.begin(), ch.M.end());
+  js.c_axes.insert(js.c_axes.end(), ch.N.begin(), ch.N.end());
+  js.kinner = (int)ch.K.size();
+  js.ninner = (int)ch.N.size();
+  for (int v : ch.batch) js.nbatch *= vres[v];
+  for (int v : ch.M) js.M *= vres[v];
+  for (int v : ch.K) js.K *= vres[v];
+  js.nbits = ch.nbits;
+  js.reshape_bits = ch.reshape_bits;
+  const BitArr& A = js.swap ? Y : X;
+  const BitArr& B = js.swap ? X : Y;
+  for (int i = 0; i < A.ndim; ++i)
+    if (!has(js.a_axes, A.vars[i])) js.private_a *= (double)A.res[i];
+  for (int i = 0; i < B.ndim; ++i)
+    if (!has(js.b_axes, B.vars[i])) js.private_b *= (double)B.res[i];
+  return js;
+}
+
+// Layout of a join's result before any final reshape.
+BitArr join_result_layout(const JoinShape& js, const std::vector<int>& keep,
+                          const std::vector<int64_t>& vres) {
+  if (js.hadamard) return make_arr(keep, vres, keep.empty() ? 0 : 1);
+  return make_arr(js.c_axes, vres, js.ninner);
+}
+
+// One two-array cluster.  When `target` is given and the result lands in its
+// layout, the result is written there.  Row-OR contractions wait in bd.pend
+// for flush_rowor.
+BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
+            const std::vector<int64_t>& vres, const BitArr* target, int64_t target_ctas) {
+  const JoinShape js = analyze_join(X, Y, keep, vres);
+  bd.st.pixel_ops_dense += js.cost;
+  bd.st.n_joins++;
+
+  if (js.hadamard) {
     bool use_target = target && target->w && target->ndim == (int)keep.size();
     for (int i = 0; use_target && i < target->ndim; ++i) use_target = has(keep, target->vars[i]);
     BitArr want = use_target ? *target : make_arr(keep, vres, keep.empty() ? 0 : 1);
@@ -324,49 +405,11 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     return out;
   }
 
-  // choose which side is A (rows) and which is B (packed columns): the one with
-  // fewer reshaped bits, then the wider packed side as B
-  struct Choice {
-    bool swap;
-    std::vector<int> batch, M, K, N;
-    double reshape_bits;
-    double nbits;
-  };
-  auto evaluate = [&](bool swap) {
-    Choice c;
-    c.swap = swap;
-    const BitArr& A = swap ? Y : X;
-    const BitArr& B = swap ? X : Y;
-    std::vector<int> av(A.vars, A.vars + A.ndim), bv(B.vars, B.vars + B.ndim);
-    classify(av, bv, c.batch, c.M, c.K, c.N);
-    std::vector<int> a_axes = c.batch, b_axes = c.batch;
-    a_axes.insert(a_axes.end(), c.M.begin(), c.M.end());
-    a_axes.insert(a_axes.end(), c.K.begin(), c.K.end());
-    b_axes.insert(b_axes.end(), c.K.begin(), c.K.end());
-    b_axes.insert(b_axes.end(), c.N.begin(), c.N.end());
-    c.reshape_bits = 0;
-    if (!same_layout(A, make_arr(a_axes, vres, (int)c.K.size()))) c.reshape_bits += (double)A.bits();
-    if (!same_layout(B, make_arr(b_axes, vres, (int)c.N.size()))) c.reshape_bits += (double)B.bits();
-    double nb = 1;
-    for (int v : c.N) nb *= (double)vres[v];
-    c.nbits = nb;
-    return c;
-  };
-  Choice c0 = evaluate(false), c1 = evaluate(true);
-  const Choice& ch = (c1.reshape_bits < c0.reshape_bits ||
-                      (c1.reshape_bits == c0.reshape_bits && c1.nbits > c0.nbits)) ? c1 : c0;
-  const BitArr& A = ch.swap ? Y : X;
-  const BitArr& B = ch.swap ? X : Y;
-  std::vector<int> a_axes = ch.batch, b_axes = ch.batch, c_axes = ch.batch;
-  a_axes.insert(a_axes.end(), ch.M.begin(), ch.M.end());
-  a_axes.insert(a_axes.end(), ch.K.begin(), ch.K.end());
-  b_axes.insert(b_axes.end(), ch.K.begin(), ch.K.end());
-  b_axes.insert(b_axes.end(), ch.N.begin(), ch.N.end());
-  c_axes.insert(c_axes.end(), ch.M.begin(), ch.M.end());
-  c_axes.insert(c_axes.end(), ch.N.begin(), ch.N.end());
-  BitArr Am = conform(bd, A, make_arr(a_axes, vres, (int)ch.K.size()));
-  BitArr Bm = conform(bd, B, make_arr(b_axes, vres, (int)ch.N.size()));
-  BitArr C = make_arr(c_axes, vres, (int)ch.N.size());
+  const BitArr& A = js.swap ? Y : X;
+  const BitArr& B = js.swap ? X : Y;
+  BitArr Am = conform(bd, A, make_arr(js.a_axes, vres, js.kinner));
+  BitArr Bm = conform(bd, B, make_arr(js.b_axes, vres, js.ninner));
+  BitArr C = make_arr(js.c_axes, vres, js.ninner);
   if (target && target->w && same_layout(C, *target)) C.w = target->w;
   else C.w = bd.alloc_words(C.words());
 
@@ -375,12 +418,9 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
   d.A = Am.w;
   d.B = Bm.w;
   d.C = C.w;
-  d.nbatch = 1;
-  for (int v : ch.batch) d.nbatch *= vres[v];
-  d.M = 1;
-  for (int v : ch.M) d.M *= vres[v];
-  d.K = 1;
-  for (int v : ch.K) d.K *= vres[v];
+  d.nbatch = js.nbatch;
+  d.M = js.M;
+  d.K = js.K;
   d.Nw = Bm.row_words();
   d.a_row_words = Am.row_words();
   d.err = bd.d_err;
@@ -589,12 +629,14 @@ struct Network {
   int order;
   const int32_t* pairs;
   BitArr target;
+  std::vector<int32_t> own_pairs;  // orders chosen by the learned planner
 };
 
 // Plots of all networks in one launch pair, then their joins level by level:
 // the joins of one level of every network's cluster tree are independent and
 // share one contraction launch per tile width.
-void build_networks(Builder& bd, std::vector<Network>& nets) {
+void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_launch = false,
+                    std::vector<BitArr>* join_results = nullptr) {
   std::vector<PlotReq> reqs;
   for (auto& n : nets)
     for (int i = 0; i < n.nrel; ++i) reqs.push_back({&n.rels[i], n.axes, n.strict, nullptr});
@@ -644,8 +686,15 @@ void build_networks(Builder& bd, std::vector<Network>& nets) {
         if (s.level[nrel + t] != lv) continue;
         const Join& jn = s.plan.joins[t];
         const bool last = (t + 1 == nj);
+        const size_t first_op = bd.ops.size();
         s.slots[nrel + t] = join(bd, s.slots[jn.a], s.slots[jn.b], jn.keep, s.vres,
-                                 last ? &nets[k].target : nullptr, target_ctas);
+                                 last ? &nets[k].target : nullptr,
+                                 one_join_per_launch ? 152 : target_ctas);
+        if (one_join_per_launch) {
+          flush_rowor(bd);
+          for (size_t q = first_op; q < bd.ops.size(); ++q) bd.ops[q].join = t;
+          if (join_results) join_results->push_back(s.slots[nrel + t]);
+        }
       }
     }
     flush_rowor(bd);
@@ -816,8 +865,10 @@ void check_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel
     n.exposed.push_back(exposed[i]);
   }
   n.order = opts ? opts->order : PA_ORDER_GREEDY;
-  PA_CHECK_ARG(n.order == PA_ORDER_GREEDY || n.order == PA_ORDER_GIVEN || n.order == PA_ORDER_LEFT,
+  PA_CHECK_ARG(n.order == PA_ORDER_GREEDY || n.order == PA_ORDER_GIVEN || n.order == PA_ORDER_LEFT ||
+                   n.order == PA_ORDER_LEARNED,
                "opts: unknown order");
+  PA_CHECK_ARG(n.order != PA_ORDER_LEARNED || opts->model, "opts: PA_ORDER_LEARNED needs a model");
   n.pairs = nullptr;
   if (n.order == PA_ORDER_GIVEN) {
     PA_CHECK_ARG(plan_valid_given(nrel, opts->npairs, opts->pairs),
@@ -830,6 +881,244 @@ void check_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel
   n.nrel = nrel;
   n.rels = rels;
   n.target = from_pa(*out);
+}
+
+
+// ------------------------------------------------------------ learned order
+// Everything the cost model sees is computed here, on the host, from shapes and
+// estimated densities, so that planning never waits for the solve.
+constexpr int kFeat = PA_FEATURES;
+
+uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double nest_host(int k, int rem, const double*& cp, const double* x) {
+  if (k < 0) return *cp++;
+  double s = 0.0, pw = 1.0;
+  for (int e = 0; e <= rem; ++e) {
+    s += nest_host(k - 1, rem - e, cp, x) * pw;
+    pw *= x[k];
+  }
+  return s;
+}
+
+// Fraction of pixels a plot turns on, estimated from 512 sampled pixel centres:
+// for f = 0 by a Gaussian kernel estimate of the density of f(c) at 0 (times
+// the width 2 eps of the accepted band), for f <= 0 / f < 0 by counting.
+double estimate_density(const pa_relation& r, const pa_axis* axes, double eps) {
+  const int S = 512;
+  std::vector<int64_t> ord = nest_order(r.arity, r.degree);
+  std::vector<double> nc(ord.size());
+  for (size_t k = 0; k < ord.size(); ++k) nc[k] = r.coeffs[ord[k]];
+  std::vector<double> f(S);
+  uint64_t seed = 0x160900061ull;
+  for (int p = 0; p < r.arity; ++p) seed = mix64(seed ^ (uint64_t)axes[r.vars[p]].res);
+  for (int i = 0; i < S; ++i) {
+    double x[kMaxDim];
+    for (int p = 0; p < r.arity; ++p) {
+      const pa_axis& ax = axes[r.vars[p]];
+      const int64_t idx = (int64_t)(mix64(seed + (uint64_t)i * 16 + p) % (uint64_t)ax.res);
+      x[p] = ax.lo + ((double)idx + 0.5) * ((ax.hi - ax.lo) / (double)ax.res);
+    }
+    const double* cp = nc.data();
+    f[i] = nest_host(r.arity - 1, r.degree, cp, x);
+  }
+  int direct = 0;
+  for (double v : f)
+    direct += (r.kind == PA_EQ) ? (fabs(v) <= eps) : (v <= eps);
+  double est = (double)direct / S;
+  if (r.kind == PA_EQ) {
+    double mean = 0, var = 0;
+    for (double v : f) mean += v;
+    mean /= S;
+    for (double v : f) var += (v - mean) * (v - mean);
+    const double sd = sqrt(var / S);
+    const double h = std::max(1e-300, 1.06 * sd * pow((double)S, -0.2));
+    double acc = 0;
+    for (double v : f) acc += exp(-0.5 * (v / h) * (v / h));
+    const double pdf0 = acc / (S * h * sqrt(2.0 * M_PI));
+    est = std::max(est, std::min(1.0, 2.0 * eps * pdf0));
+  }
+  return std::min(1.0, std::max(est, 1e-6));
+}
+
+// fraction of set bits after OR-ing `n` independent entries of density rho
+double or_density(double rho, double n) {
+  if (rho >= 1.0) return 1.0;
+  return 1.0 - exp(n * log1p(-rho));
+}
+
+double lg2(double v) { return log2(std::max(v, 1e-30)); }
+
+// The cost model's inputs for one join, and the estimated density of its result.
+void join_features(const JoinShape& js, double rx, double ry, float* f, double* rho_out) {
+  double ra = js.swap ? ry : rx, rb = js.swap ? rx : ry;
+  ra = or_density(ra, js.private_a);
+  rb = or_density(rb, js.private_b);
+  double rc, work, m, n, k, batch;
+  if (js.hadamard) {
+    rc = ra * rb;
+    m = 1, n = js.result_bits, k = 1, batch = 1;
+    work = js.result_bits / 64.0;
+  } else {
+    rc = or_density(ra * rb, (double)js.K);
+    m = (double)js.M, n = js.nbits, k = (double)js.K, batch = (double)js.nbatch;
+    work = ra * m * k * batch * ceil(n / 64.0);
+  }
+  f[0] = (float)(lg2(m) / 16);
+  f[1] = (float)(lg2(n) / 16);
+  f[2] = (float)(lg2(k) / 16);
+  f[3] = (float)(lg2(batch) / 16);
+  f[4] = (float)(lg2(1 + js.reshape_bits) / 32);
+  f[5] = (float)(lg2(js.cost) / 48);
+  f[6] = (float)(lg2(js.result_bits) / 32);
+  f[7] = (float)ra;
+  f[8] = (float)rb;
+  f[9] = (float)(lg2(ra + 1e-9) / 30);
+  f[10] = (float)(lg2(rb + 1e-9) / 30);
+  f[11] = (float)(lg2(1 + work) / 40);
+  f[12] = (float)(lg2(1 + rc * js.result_bits) / 32);
+  f[13] = js.hadamard ? 1.0f : 0.0f;
+  f[14] = (float)(lg2(js.private_a * js.private_b) / 32);
+  f[15] = 1.0f;
+  if (rho_out) *rho_out = rc;
+}
+
+struct SimResult {
+  std::vector<float> feats;  // one row of kFeat per join
+  double peak_bits = 0;
+};
+
+// Walk a plan on the host: layouts as join() would build them, densities
+// propagated from the plot estimates.
+SimResult simulate_plan(const Network& n, const Plan& plan, const std::vector<double>& plot_dens) {
+  SimResult r;
+  std::vector<int64_t> vres(n.nvars);
+  for (int v = 0; v < n.nvars; ++v) vres[v] = n.axes[v].res;
+  std::vector<BitArr> slots;
+  std::vector<double> dens;
+  for (int i = 0; i < n.nrel; ++i) {
+    std::vector<int> dv = distinct_vars(n.rels[i]);
+    slots.push_back(make_arr(dv, vres, 1));
+    dens.push_back(plot_dens[i]);
+  }
+  for (const Join& jn : plan.joins) {
+    const JoinShape js = analyze_join(slots[jn.a], slots[jn.b], jn.keep, vres);
+    float f[kFeat];
+    double rc = 0;
+    join_features(js, dens[jn.a], dens[jn.b], f, &rc);
+    r.feats.insert(r.feats.end(), f, f + kFeat);
+    r.peak_bits = std::max(r.peak_bits, js.result_bits);
+    slots.push_back(join_result_layout(js, jn.keep, vres));
+    dens.push_back(rc);
+  }
+  return r;
+}
+
+Plan plan_of(const Network& n, int order, const int32_t* pairs, uint64_t policy) {
+  std::vector<double> vresd(n.nvars);
+  for (int v = 0; v < n.nvars; ++v) vresd[v] = n.axes[v].res;
+  std::vector<std::vector<int>> rv;
+  for (int i = 0; i < n.nrel; ++i) rv.push_back(distinct_vars(n.rels[i]));
+  return plan_joins_policy(n.nvars, vresd, rv, n.exposed, order, pairs, policy);
+}
+
+std::vector<double> plot_densities(const Network& n) {
+  std::vector<double> d;
+  for (int i = 0; i < n.nrel; ++i)
+    d.push_back(estimate_density(n.rels[i], n.axes, relation_eps(n.rels[i], n.axes)));
+  return d;
+}
+
+struct LearnedChoice {
+  std::vector<int32_t> pairs;
+  bool learned = false;
+  float pred_chosen = 0, pred_greedy = 0;
+};
+
+std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector<Network>& nets,
+                                        int ncand) {
+  if (ncand <= 0) ncand = 16;
+  struct Cand {
+    size_t net;
+    Plan plan;
+    size_t row0, rows;
+    double peak;
+  };
+  std::vector<Cand> cands;
+  std::vector<float> X;
+  std::vector<size_t> first(nets.size());
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const Network& n = nets[k];
+    first[k] = cands.size();
+    const std::vector<double> dens = plot_densities(n);
+    std::vector<std::vector<int32_t>> seen;
+    for (int c = 0; c < ncand; ++c) {
+      Plan p = (c == 0) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 0)
+               : (c == 1) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 1)
+               : (c == 2) ? plan_of(n, PA_ORDER_LEFT, nullptr, 0)
+                          : plan_of(n, PA_ORDER_GREEDY, nullptr, 2 + (uint64_t)c * 7919 + k);
+      std::vector<int32_t> key;
+      for (const Join& j : p.joins) {
+        key.push_back(j.a);
+        key.push_back(j.b);
+      }
+      if (c > 0 && std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+      seen.push_back(key);
+      SimResult sim = simulate_plan(n, p, dens);
+      Cand cd{k, p, X.size() / kFeat, sim.feats.size() / kFeat, sim.peak_bits};
+      X.insert(X.end(), sim.feats.begin(), sim.feats.end());
+      cands.push_back(cd);
+    }
+  }
+  const int nrows = (int)(X.size() / kFeat);
+  std::vector<float> Y(nrows, 0.0f);
+  if (nrows > 0) {
+    float *dX = nullptr, *dY = nullptr;
+    check_cuda(ctx, cudaMalloc(&dX, X.size() * 4), "cudaMalloc");
+    cudaError_t e = cudaMalloc(&dY, (size_t)nrows * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dX, X.data(), X.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mlp->forward(dX, nrows, dY, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(Y.data(), dY, (size_t)nrows * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dX);
+    if (dY) cudaFree(dY);
+    check_cuda(ctx, e, "cost model forward");
+  }
+  std::vector<LearnedChoice> out(nets.size());
+  for (size_t k = 0; k < nets.size(); ++k) {
+    const size_t c0 = first[k], c1 = (k + 1 < nets.size()) ? first[k + 1] : cands.size();
+    auto total = [&](const Cand& cd) {
+      double t = 0;
+      for (size_t r = cd.row0; r < cd.row0 + cd.rows; ++r) t += exp2(8.0 * (double)Y[r]);
+      return t;
+    };
+    const double tg = total(cands[c0]);
+    size_t best = c0;
+    double tb = tg;
+    for (size_t c = c0 + 1; c < c1; ++c) {
+      const double t = total(cands[c]);
+      if (t < tb) {
+        tb = t;
+        best = c;
+      }
+    }
+    // the greedy order judges: keep the learned one only when it is predicted
+    // faster and its largest intermediate stays within 4x the greedy one
+    const bool take = best != c0 && tb < tg && cands[best].peak <= 4.0 * cands[c0].peak;
+    const Cand& ch = take ? cands[best] : cands[c0];
+    for (const Join& j : ch.plan.joins) {
+      out[k].pairs.push_back(j.a);
+      out[k].pairs.push_back(j.b);
+    }
+    out[k].learned = take;
+    out[k].pred_chosen = (float)(take ? tb : tg);
+    out[k].pred_greedy = (float)tg;
+  }
+  return out;
 }
 
 }  // namespace
@@ -849,6 +1138,28 @@ struct pa_batch {
   cudaGraphExec_t exec = nullptr;
   pa_stats st{};
 };
+
+struct pa_mlp {
+  pa_ctx* ctx = nullptr;
+  Mlp* net = nullptr;
+};
+
+// Replace PA_ORDER_LEARNED by the orders the cost model picks (given pairs).
+static pa_status resolve_learned(pa_ctx* ctx, const pa_options* opts, std::vector<Network>& nets) {
+  if (!opts || opts->order != PA_ORDER_LEARNED) return PA_OK;
+  try {
+    check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<LearnedChoice> ch = plan_learned(ctx, opts->model->net, nets, opts->ncand);
+    for (size_t k = 0; k < nets.size(); ++k) {
+      nets[k].own_pairs = ch[k].pairs;
+      nets[k].order = PA_ORDER_GIVEN;
+      nets[k].pairs = nets[k].own_pairs.data();
+    }
+    return PA_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
 
 // ================================================================ C ABI
 extern "C" {
@@ -1067,6 +1378,8 @@ pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int3
   } catch (const Fail& f) {
     return f.st;
   }
+  pa_status st = resolve_learned(ctx, opts, nets);
+  if (st != PA_OK) return st;
   return run_call(ctx, static_cast<cudaStream_t>(stream), stats,
                   [&](Builder& bd) { build_networks(bd, nets); });
 }
@@ -1082,10 +1395,10 @@ static pa_status check_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems
       check_network(ctx, s.nvars, s.axes, s.nrel, s.rels, s.nexposed, s.exposed, opts, &outs[k],
                     nets[k]);
     }
-    return PA_OK;
   } catch (const Fail& f) {
     return f.st;
   }
+  return resolve_learned(ctx, opts, nets);
 }
 
 pa_status pa_solve_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
@@ -1206,6 +1519,226 @@ void pa_batch_destroy(pa_batch* bt) {
   }
   if (bt->h_blob) cudaFreeHost(bt->h_blob);
   delete bt;
+}
+
+pa_status pa_mlp_create(pa_ctx* ctx, int32_t hidden, int32_t nlayers, uint64_t seed,
+                        pa_mlp** model) {
+  if (!ctx || !model || hidden < 1 || hidden > 1024 || nlayers < 0 || nlayers > 8)
+    return PA_ERR_INVALID_ARG;
+  *model = nullptr;
+  cudaSetDevice(ctx->device);
+  pa_mlp* m = new pa_mlp();
+  m->ctx = ctx;
+  m->net = new Mlp(PA_FEATURES, hidden, nlayers);
+  if (m->net->alloc_params() != cudaSuccess) {
+    cudaGetLastError();
+    pa_mlp_destroy(m);
+    return set_err(ctx, PA_ERR_OOM, "cost model: cudaMalloc failed");
+  }
+  // He-uniform weights from a SplitMix64 stream, zero biases
+  std::vector<float> p(m->net->np, 0.0f);
+  uint64_t st = seed;
+  for (size_t l = 0; l + 1 < m->net->sizes.size(); ++l) {
+    const int ni = m->net->sizes[l], no = m->net->sizes[l + 1];
+    const double lim = sqrt(6.0 / ni);
+    for (int64_t k = 0; k < (int64_t)no * ni; ++k) {
+      const uint64_t z = mix64(st++);
+      const double u = (double)(z >> 11) * 0x1p-53;
+      p[m->net->woff[l] + k] = (float)((2.0 * u - 1.0) * lim);
+    }
+  }
+  if (cudaMemcpy(m->net->p, p.data(), p.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    pa_mlp_destroy(m);
+    return set_err(ctx, PA_ERR_CUDA, "cost model: parameter upload failed");
+  }
+  *model = m;
+  return PA_OK;
+}
+
+void pa_mlp_destroy(pa_mlp* model) {
+  if (!model) return;
+  if (model->ctx) cudaSetDevice(model->ctx->device);
+  delete model->net;
+  delete model;
+}
+
+int64_t pa_mlp_num_params(const pa_mlp* model) { return model ? model->net->np : -1; }
+
+static pa_status mlp_copy(const pa_mlp* model, void* dst, const void* src, size_t bytes,
+                          cudaMemcpyKind kind) {
+  if (!model || !dst || !src) return PA_ERR_INVALID_ARG;
+  cudaSetDevice(model->ctx->device);
+  if (cudaMemcpy(dst, src, bytes, kind) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(model->ctx, PA_ERR_CUDA, "cost model: copy failed");
+  }
+  return PA_OK;
+}
+
+pa_status pa_mlp_get_params(const pa_mlp* model, float* params) {
+  if (!model) return PA_ERR_INVALID_ARG;
+  return mlp_copy(model, params, model->net->p, model->net->np * 4, cudaMemcpyDeviceToHost);
+}
+
+pa_status pa_mlp_set_params(pa_mlp* model, const float* params) {
+  if (!model) return PA_ERR_INVALID_ARG;
+  return mlp_copy(model, model->net->p, params, model->net->np * 4, cudaMemcpyHostToDevice);
+}
+
+pa_status pa_mlp_get_grads(const pa_mlp* model, float* grads) {
+  if (!model) return PA_ERR_INVALID_ARG;
+  return mlp_copy(model, grads, model->net->g, model->net->np * 4, cudaMemcpyDeviceToHost);
+}
+
+pa_status pa_mlp_forward(pa_mlp* model, const float* x, int32_t n, float* y, void* stream) {
+  if (!model || !x || !y || n < 0) return PA_ERR_INVALID_ARG;
+  if (n == 0) return PA_OK;
+  cudaSetDevice(model->ctx->device);
+  if (model->net->forward(x, n, y, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(model->ctx, PA_ERR_CUDA, "cost model: forward failed");
+  }
+  return PA_OK;
+}
+
+pa_status pa_mlp_backward(pa_mlp* model, const float* x, const float* t, int32_t n, float* loss,
+                          void* stream) {
+  if (!model || !x || !t || n <= 0) return PA_ERR_INVALID_ARG;
+  cudaSetDevice(model->ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (model->net->backward(x, t, n, s) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(model->ctx, PA_ERR_CUDA, "cost model: backward failed");
+  }
+  if (loss) {
+    if (cudaMemcpyAsync(loss, model->net->loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(model->ctx, PA_ERR_CUDA, "cost model: loss read failed");
+    }
+  }
+  return PA_OK;
+}
+
+pa_status pa_mlp_adam(pa_mlp* model, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!model || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return PA_ERR_INVALID_ARG;
+  cudaSetDevice(model->ctx->device);
+  if (model->net->adam(lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(model->ctx, PA_ERR_CUDA, "cost model: adam failed");
+  }
+  return PA_OK;
+}
+
+pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts, pa_array* out,
+                      int32_t max_joins, float* features, float* micros, float* densities,
+                      int32_t* njoins, void* stream) {
+  if (!ctx || !sys || !njoins || max_joins < 0 ||
+      (max_joins > 0 && (!features || !micros || !densities)))
+    return PA_ERR_INVALID_ARG;
+  std::vector<Network> nets(1);
+  try {
+    check_network(ctx, sys->nvars, sys->axes, sys->nrel, sys->rels, sys->nexposed, sys->exposed,
+                  opts, out, nets[0]);
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  pa_status st = resolve_learned(ctx, opts, nets);
+  if (st != PA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* dcnt = nullptr;
+  std::vector<cudaEvent_t> evs;
+  try {
+    check_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    Builder dry(ctx, true, nullptr, 0);
+    build_networks(dry, nets, true);
+    const size_t blob_cap = round_up(dry.blob.size() + 64, kAlign);
+    st = ensure_arena(ctx, dry.used + blob_cap + kAlign);
+    if (st != PA_OK) return st;
+    Builder bd(ctx, false, ctx->arena, blob_cap);
+    bd.d_err = ctx->d_err;
+    std::vector<BitArr> results;
+    build_networks(bd, nets, true, &results);
+    upload_blob(ctx, bd.blob, s);
+    // one event pair per op
+    const size_t nops = bd.ops.size();
+    evs.resize(2 * nops, nullptr);
+    for (auto& e : evs) check_cuda(ctx, cudaEventCreate(&e), "cudaEventCreate");
+    for (size_t q = 0; q < nops; ++q) {
+      std::vector<Op> one(1, bd.ops[q]);
+      check_cuda(ctx, cudaEventRecord(evs[2 * q], s), "cudaEventRecord");
+      run_ops(ctx, one, ctx->arena, s, false);
+      check_cuda(ctx, cudaEventRecord(evs[2 * q + 1], s), "cudaEventRecord");
+    }
+    const int nj = (int)results.size();
+    check_cuda(ctx, cudaMalloc(&dcnt, std::max(1, nj) * sizeof(unsigned long long)), "cudaMalloc");
+    check_cuda(ctx, cudaMemsetAsync(dcnt, 0, std::max(1, nj) * sizeof(unsigned long long), s),
+               "cudaMemsetAsync");
+    for (int t = 0; t < nj; ++t) launch_popcount(results[t].w, results[t].words(), dcnt + t, s);
+    check_cuda(ctx, cudaGetLastError(), "popcount_kernel");
+    std::vector<unsigned long long> cnt(std::max(1, nj));
+    check_cuda(ctx, cudaMemcpyAsync(cnt.data(), dcnt, cnt.size() * 8, cudaMemcpyDeviceToHost, s),
+               "cudaMemcpyAsync");
+    check_cuda(ctx, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    std::vector<double> us(nj, 0.0);
+    for (size_t q = 0; q < nops; ++q) {
+      float ms = 0;
+      check_cuda(ctx, cudaEventElapsedTime(&ms, evs[2 * q], evs[2 * q + 1]), "cudaEventElapsedTime");
+      if (bd.ops[q].join >= 0 && bd.ops[q].join < nj) us[bd.ops[q].join] += 1000.0 * ms;
+    }
+    const Plan plan = plan_of(nets[0], nets[0].order, nets[0].pairs, 0);
+    const SimResult sim = simulate_plan(nets[0], plan, plot_densities(nets[0]));
+    *njoins = nj;
+    for (int t = 0; t < nj && t < max_joins; ++t) {
+      for (int k = 0; k < kFeat; ++k) features[t * kFeat + k] = sim.feats[t * kFeat + k];
+      micros[t] = (float)us[t];
+      densities[t] = (float)((double)cnt[t] / (double)std::max<int64_t>(1, results[t].bits()));
+    }
+  } catch (const Fail& f) {
+    st = f.st;
+  }
+  if (dcnt) cudaFree(dcnt);
+  for (auto e : evs)
+    if (e) cudaEventDestroy(e);
+  return st;
+}
+
+pa_status pa_plan_learned(pa_ctx* ctx, const pa_mlp* model, int32_t nsys, const pa_system* systems,
+                          int32_t ncand, int32_t* pairs_out, int32_t* learned, float* pred_us) {
+  if (!ctx || !model || nsys < 1 || !systems || !pairs_out || !learned || !pred_us)
+    return PA_ERR_INVALID_ARG;
+  std::vector<Network> nets(nsys);
+  try {
+    for (int k = 0; k < nsys; ++k) {
+      const pa_system& sy = systems[k];
+      check_axes(ctx, sy.nvars, sy.axes);
+      PA_CHECK_ARG(sy.nrel >= 1 && sy.rels, "at least one relation");
+      for (int i = 0; i < sy.nrel; ++i) check_relation(ctx, sy.rels[i], sy.nvars);
+      Network& n = nets[k];
+      n.nvars = sy.nvars;
+      n.axes = sy.axes;
+      n.nrel = sy.nrel;
+      n.rels = sy.rels;
+      n.exposed.assign(sy.exposed, sy.exposed + sy.nexposed);
+      for (int v : n.exposed) PA_CHECK_ARG(v >= 0 && v < sy.nvars, "exposed: variable out of range");
+      n.order = PA_ORDER_GREEDY;
+      n.pairs = nullptr;
+      n.strict = 0;
+    }
+    std::vector<LearnedChoice> ch = plan_learned(ctx, model->net, nets, ncand);
+    size_t off = 0;
+    for (int k = 0; k < nsys; ++k) {
+      for (int32_t v : ch[k].pairs) pairs_out[off++] = v;
+      learned[k] = ch[k].learned ? 1 : 0;
+      pred_us[2 * k] = ch[k].pred_chosen;
+      pred_us[2 * k + 1] = ch[k].pred_greedy;
+    }
+    return PA_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
 }
 
 pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const pa_relation* rels,

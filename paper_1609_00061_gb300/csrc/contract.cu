@@ -396,6 +396,24 @@ cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
   return cudaGetLastError();
 }
 
+// -------------------------------------------------------------- popcount
+__global__ void popcount_kernel(const uint64_t* __restrict__ w, int64_t n,
+                                unsigned long long* __restrict__ out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += (unsigned long long)__popcll(w[i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void launch_popcount(const uint64_t* w, int64_t nwords, unsigned long long* out, cudaStream_t s) {
+  if (nwords <= 0) return;
+  int64_t blocks = (nwords + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  popcount_kernel<<<(unsigned)blocks, 256, 0, s>>>(w, nwords, out);
+}
+
 // ------------------------------------------------------------------- AND
 __global__ void and_kernel(const uint64_t* __restrict__ a, const uint64_t* __restrict__ b,
                            uint64_t* __restrict__ c, int64_t n) {

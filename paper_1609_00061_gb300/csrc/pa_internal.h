@@ -138,6 +138,8 @@ cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
 // cudaSuccess when this build holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
+// *out += number of set bits in w[0..nwords) (padding bits are zero)
+void launch_popcount(const uint64_t* w, int64_t nwords, unsigned long long* out, cudaStream_t s);
 
 // ----------------------------------------------------------- host helpers
 int64_t coeff_count(int n, int degree);

@@ -132,6 +132,23 @@ static std::vector<int> set_union(const std::vector<int>& a, const std::vector<i
 Plan plan_joins(int nvars, const std::vector<double>& vres,
                 const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
                 int order, const int32_t* given_pairs) {
+  return plan_joins_policy(nvars, vres, rel_vars, exposed, order, given_pairs, 0);
+}
+
+// policy (order == PA_ORDER_GREEDY): 0 greedy as documented; 1 smallest cost
+// r^Lambda first; 2 + seed: at every step a seeded random pick among the three
+// best greedy pairs (candidate orders for the learned cost model).
+Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
+                       const std::vector<std::vector<int>>& rel_vars,
+                       const std::vector<int>& exposed, int order, const int32_t* given_pairs,
+                       uint64_t policy) {
+  uint64_t rng = policy * 0x9E3779B97F4A7C15ull + 0x160900061ull;
+  auto next_rand = [&rng]() {
+    uint64_t z = (rng += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
   Plan plan;
   int nrel = (int)rel_vars.size();
   // live slots: slot id -> variable set
@@ -175,23 +192,29 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
       // smallest result, then smallest cost r^Lambda, then the shallower pair:
       // among equal joins the tree stays balanced, so that independent joins
       // can run side by side (the parallel cost of Sec. 3.5)
-      double best_size = 0, best_cost = 0;
-      int best_depth = 0;
+      struct Cand {
+        double k1, k2;
+        int dep, x, y;
+      };
+      std::vector<Cand> cands;
       for (size_t i = 0; i < live.size(); ++i)
         for (size_t j = i + 1; j < live.size(); ++j) {
           int x = live[i], y = live[j];
           double size = set_size(keep_of(x, y), vres);
           double cost = set_size(set_union(slot_vars[x], slot_vars[y]), vres);
           int dep = std::max(depth[x], depth[y]);
-          if (a < 0 || size < best_size || (size == best_size && cost < best_cost) ||
-              (size == best_size && cost == best_cost && dep < best_depth)) {
-            a = x;
-            b = y;
-            best_size = size;
-            best_cost = cost;
-            best_depth = dep;
-          }
+          if (policy == 1) cands.push_back({cost, size, dep, x, y});
+          else cands.push_back({size, cost, dep, x, y});
         }
+      std::stable_sort(cands.begin(), cands.end(), [](const Cand& p, const Cand& q) {
+        if (p.k1 != q.k1) return p.k1 < q.k1;
+        if (p.k2 != q.k2) return p.k2 < q.k2;
+        return p.dep < q.dep;
+      });
+      size_t pick = 0;
+      if (policy >= 2 && cands.size() > 1) pick = next_rand() % std::min<size_t>(3, cands.size());
+      a = cands[pick].x;
+      b = cands[pick].y;
     }
     Join jn;
     jn.a = a;

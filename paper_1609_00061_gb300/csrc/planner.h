@@ -26,6 +26,10 @@ struct Plan {
 Plan plan_joins(int nvars, const std::vector<double>& vres,
                 const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
                 int order, const int32_t* given_pairs);
+Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
+                       const std::vector<std::vector<int>>& rel_vars,
+                       const std::vector<int>& exposed, int order, const int32_t* given_pairs,
+                       uint64_t policy);
 bool plan_valid_given(int nrel, int npairs, const int32_t* pairs);
 
 pa_status tree_cost(int32_t nlinks, const double* link_res, int32_t npacks,

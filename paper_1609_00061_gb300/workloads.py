@@ -154,32 +154,39 @@ def batched_chains(nsys: int = 4096, seed: int = SEED_BASE + 4, res_choices=None
 
 
 def random_network(rng: SplitMix64, nvars_range=(10, 16), nrel_range=(12, 20),
-                   res_choices=(128, 256, 512), nexp_range=(2, 3), lo=-2.0, hi=2.0) -> System:
-    """A random relation network: every variable used, arities 2-3, cubics."""
+                   res_choices=(128, 256, 512), nexp_range=(2, 3), lo=-2.0, hi=2.0,
+                   window=4) -> System:
+    """A random relation network: nrel relations of arity 2-3 (cubics with N(0,1)
+    coefficients) over nvars variables on a line, each relation drawing its
+    variables from a window of `window` consecutive ones (so the network stays
+    tree-like), every variable used at least once, 2-3 exposed variables."""
     nv = int(rng.integers(nvars_range[0], nvars_range[1], 1)[0])
     nr = int(rng.integers(nrel_range[0], nrel_range[1], 1)[0])
     res = int(res_choices[int(rng.integers(0, len(res_choices) - 1, 1)[0])])
     rels = []
-    used = set()
-    for k in range(nr):
+    # a path through all variables first, so every one is used and linked
+    for k in range(nv - 1):
+        if len(rels) >= nr:
+            break
+        if k + 2 < nv and rng.uniform(1)[0] < 0.35:
+            vs = (k, k + 1, k + 2)
+        else:
+            vs = (k, k + 1)
+        rels.append(Relation(vs, 3, random_cubic(rng, len(vs))))
+    covered = set(v for r in rels for v in r.vars)
+    for v in range(nv):
+        if v not in covered:
+            rels.append(Relation((v - 1, v), 3, random_cubic(rng, 2)))
+    while len(rels) < nr:
+        s0 = int(rng.integers(0, max(0, nv - window), 1)[0])
         ar = int(rng.integers(2, 3, 1)[0])
+        pool = list(range(s0, min(nv, s0 + window)))
         vs = []
         while len(vs) < ar:
-            # later relations prefer variables not used yet, so every variable occurs
-            unused = [v for v in range(nv) if v not in used and v not in vs]
-            if unused and rng.uniform(1)[0] < 0.5:
-                v = unused[int(rng.integers(0, len(unused) - 1, 1)[0])]
-            else:
-                v = int(rng.integers(0, nv - 1, 1)[0])
+            v = pool[int(rng.integers(0, len(pool) - 1, 1)[0])]
             if v not in vs:
                 vs.append(v)
-        used.update(vs)
         rels.append(Relation(tuple(vs), 3, random_cubic(rng, ar)))
-    for v in range(nv):
-        if v not in used:
-            # attach an unused variable to the last relation's first partner
-            w = rels[-1].vars[0] if rels[-1].vars[0] != v else rels[-1].vars[1]
-            rels.append(Relation((w, v), 3, random_cubic(rng, 2)))
     ne = int(rng.integers(nexp_range[0], nexp_range[1], 1)[0])
     exposed = []
     while len(exposed) < ne:
@@ -188,6 +195,11 @@ def random_network(rng: SplitMix64, nvars_range=(10, 16), nrel_range=(12, 20),
             exposed.append(v)
     axes = [(lo, hi, res)] * nv
     return System(f"net_v{nv}_r{len(rels)}_res{res}", axes, rels, tuple(exposed))
+
+
+def random_networks(n: int, seed: int = SEED_BASE + 5, **kw) -> list:
+    rng = SplitMix64(seed)
+    return [random_network(rng, **kw) for _ in range(n)]
 
 
 def workload(name: str, **kw):

@@ -394,3 +394,33 @@ def test_circle_parabola_roots_exposed_x(orc):
 def test_entries_count_example():
     """Sec. 3.1: a pack with three ports of resolution 20 has 20^3 = 8000 entries."""
     assert np.zeros((20, 20, 20), np.uint8).size == 8000
+
+
+# --------------------------------------------------------- cost-model oracle
+def test_mlp_oracle_gradient_central_differences():
+    """The oracle's analytic gradient against central differences of its loss."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(21)
+    sizes = M.layer_sizes(16, 12, 3)
+    npar = sum(sizes[i + 1] * sizes[i] + sizes[i + 1] for i in range(len(sizes) - 1))
+    p = rng.normal(size=npar) * 0.4
+    X = rng.normal(size=(37, 16))
+    T = rng.normal(size=37)
+    L, g = M.loss_and_grad(p, sizes, X, T)
+    assert abs(L - M.loss(p, sizes, X, T)) < 1e-12
+    h = 1e-6
+    for k in rng.choice(npar, 60, replace=False):
+        e = np.zeros(npar)
+        e[k] = h
+        num = (M.loss(p + e, sizes, X, T) - M.loss(p - e, sizes, X, T)) / (2 * h)
+        assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(num)), k
+
+
+def test_mlp_oracle_forward_by_hand():
+    """A 1-input, one-hidden-unit network computed by hand."""
+    from oracle import mlp as M
+    sizes = [1, 1, 1]
+    # W1 = 2, b1 = -1, W2 = 3, b2 = 0.5: y = 3 * relu(2x - 1) + 0.5
+    p = np.array([2.0, -1.0, 3.0, 0.5])
+    y = M.forward(p, sizes, np.array([[0.0], [1.0], [2.0]]))
+    assert y.tolist() == [0.5, 3.5, 9.5]
