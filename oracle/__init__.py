@@ -206,26 +206,55 @@ def reduce(X: Arr, keep, vres) -> Arr:
     return contract(X, one, keep, vres)
 
 
-def solve(axes, rels, exposed, strict: bool = False, order=None) -> Arr:
+def solve(axes, rels, exposed, strict: bool = False, order=None, smallest: bool = None) -> Arr:
     """The pixel array method end to end (Sec. 3.6).
 
-    Plots every relation, then clusters one array at a time into a running
-    product (left to right, or in ``order``), summing out each variable as soon
-    as no array still to come and no exposed variable uses it.  Any cluster tree
-    gives the same result (Sec. 3.3, associativity), so the order is the
-    simplest one."""
+    Plots every relation, then joins arrays two at a time, summing out each
+    variable as soon as no array still to be joined and no exposed variable
+    uses it.  Any cluster tree gives the same result (Sec. 3.3, associativity);
+    the tree only decides how large the intermediate arrays get:
+      - order given: fold the plots into a running product in that order;
+      - otherwise, with few relations (<= 4) fold left to right;
+      - otherwise join, at every step, the two arrays whose result is smallest
+        (so that loosely coupled networks stay small)."""
     vres = [int(a[2]) for a in axes]
     exposed = tuple(int(v) for v in exposed)
     plots = [plot_relation(r, axes, strict) for r in rels]
-    seq = list(range(len(plots))) if order is None else list(order)
-    acc = Arr(np.ones((), dtype=np.uint8), ())
-    for pos, i in enumerate(seq):
-        later = set(exposed)
-        for j in seq[pos + 1:]:
-            later.update(plots[j].vars)
-        have = []
-        for v in tuple(acc.vars) + tuple(plots[i].vars):
-            if v in later and v not in have:
-                have.append(v)
-        acc = contract(acc, plots[i], tuple(have), vres)
-    return contract(acc, Arr(np.ones((), dtype=np.uint8), ()), exposed, vres)
+    if smallest is None:
+        smallest = order is None and len(plots) > 4
+    one = Arr(np.ones((), dtype=np.uint8), ())
+    if not smallest:
+        seq = list(range(len(plots))) if order is None else list(order)
+        acc = one
+        for pos, i in enumerate(seq):
+            later = set(exposed)
+            for j in seq[pos + 1:]:
+                later.update(plots[j].vars)
+            have = []
+            for v in tuple(acc.vars) + tuple(plots[i].vars):
+                if v in later and v not in have:
+                    have.append(v)
+            acc = contract(acc, plots[i], tuple(have), vres)
+        return contract(acc, one, exposed, vres)
+    live = list(plots)
+    while len(live) > 1:
+        best = None
+        for i in range(len(live)):
+            for j in range(i + 1, len(live)):
+                later = set(exposed)
+                for k, a in enumerate(live):
+                    if k != i and k != j:
+                        later.update(a.vars)
+                keep = []
+                for v in tuple(live[i].vars) + tuple(live[j].vars):
+                    if v in later and v not in keep:
+                        keep.append(v)
+                size = 1
+                for v in keep:
+                    size *= vres[v]
+                if best is None or size < best[0]:
+                    best = (size, i, j, tuple(keep))
+        _, i, j, keep = best
+        joined = contract(live[i], live[j], keep, vres)
+        live = [a for k, a in enumerate(live) if k not in (i, j)] + [joined]
+    return contract(live[0], one, exposed, vres)

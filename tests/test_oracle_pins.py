@@ -424,3 +424,14 @@ def test_mlp_oracle_forward_by_hand():
     p = np.array([2.0, -1.0, 3.0, 0.5])
     y = M.forward(p, sizes, np.array([[0.0], [1.0], [2.0]]))
     assert y.tolist() == [0.5, 3.5, 9.5]
+
+
+def test_solve_strategies_agree():
+    """Smallest-result pairwise joining and left-to-right folding give the same
+    array (associativity), on a tree-like random network."""
+    import oracle
+    net = W.random_networks(1, seed=9, nvars_range=(7, 8), nrel_range=(8, 9),
+                            res_choices=(12,))[0]
+    a = oracle.solve(net.axes, net.rels, net.exposed, smallest=True).data
+    b = oracle.solve(net.axes, net.rels, net.exposed, smallest=False).data
+    assert np.array_equal(a, b)
