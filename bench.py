@@ -244,6 +244,75 @@ def run_batched(eng, pa, W, dev, reps=5):
                       "plain: host clock around the per-system calls, synchronised"}
 
 
+def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
+    """Random relation networks (10-16 variables, 12-20 relations of arity 2-3,
+    128/256/512 px per axis, 2-3 exposed): the cost model is trained on solver
+    logs of disjoint training networks, then the evaluation networks are solved
+    (a) one pa_solve_network call each, greedy order; (b) as one graph-captured
+    batch, greedy order; (c) as one graph-captured batch, learned order."""
+    import torch
+    from paper_1609_00061_gb300 import learned as L
+
+    def usable(nets):
+        keep = []
+        for n in nets:
+            _, ops, peak = pa.pa_plan_order(n.axes, n.rels, n.exposed)
+            if peak <= (1 << 30) and ops <= 1e13:
+                keep.append(n)
+        return keep
+
+    t0 = time.perf_counter()
+    train = usable(W.random_networks(n_train, seed=W.SEED_BASE + 50))
+    X, T, D = L.collect_logs(eng, train, orders_per_system=3, seed=2)
+    model = pa.CostModel(eng, hidden=128, nlayers=3, seed=W.SEED_BASE + 5)
+    hist = model.train(X, T, epochs=150, batch=256, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    nets = usable(W.random_networks(n_eval, seed=W.SEED_BASE + 5))
+    stream = torch.cuda.current_stream()
+
+    def time_batch(order):
+        b = eng.batch(nets, order=order, model=model if order == "learned" else None)
+        for _ in range(2):
+            b.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = b.stats()
+        b.close()
+        return e0.elapsed_time(e1) / 1e3 / reps, st
+
+    g_s, g_st = time_batch("greedy")
+    l_s, l_st = time_batch("learned")
+    _, learned_flags, pred = eng.plan_learned(model, nets)
+    outs = [pa.BitArray.empty(n.exposed, [n.axes[v][2] for v in n.exposed], eng.device)
+            for n in nets]
+    for n, o in zip(nets[:16], outs[:16]):
+        pa.pa_solve_network(eng.ctx, n.axes, n.rels, n.exposed, o)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for n, o in zip(nets, outs):
+        pa.pa_solve_network(eng.ctx, n.axes, n.rels, n.exposed, o)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t1
+    model.close()
+    return {"workload": "random relation networks: 10-16 vars, 12-20 relations of arity 2-3, "
+                        "cubics N(0,1), 128/256/512 px per axis, 2-3 exposed, seed 0x160900061+5",
+            "networks": len(nets), "train_networks": len(train), "train_samples": int(len(T)),
+            "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
+            "plain_greedy_systems_per_s": len(nets) / plain_s,
+            "batched_greedy_systems_per_s": len(nets) / g_s,
+            "batched_learned_systems_per_s": len(nets) / l_s,
+            "learned_vs_plain": plain_s / l_s, "learned_vs_batched_greedy": g_s / l_s,
+            "learned_orders_kept": int(sum(learned_flags)),
+            "pixel_ops_dense_greedy": g_st["pixel_ops_dense"],
+            "pixel_ops_dense_learned": l_st["pixel_ops_dense"],
+            "timing": "batched: CUDA events around graph replays; plain: host clock, synchronised"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1609_00061_gb300 as pa
@@ -334,6 +403,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_batched:
         line["batched"] = run_batched(eng, pa, W, dev)
+        line["learned"] = run_learned(eng, pa, W)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
