@@ -66,13 +66,14 @@ pa_status set_err(pa_ctx* ctx, pa_status st, const std::string& msg) {
 bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
 // ------------------------------------------------------------ program
-enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR };
+enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT };
 
 struct Op {
   OpKind kind;
   size_t off0 = 0, off1 = 0, off2 = 0;  // blob offsets (plot jobs; rowor descs, maps, cta0)
   int n = 0;                            // plot jobs / rowor problems
-  int64_t count = 0;                    // prep items / plot tiles / rowor grid / words
+  int64_t count = 0;                    // prep items / plot tiles / rowor grid / words / rows
+  int64_t m = 0, nw = 0;                // outer: M and words per row
   int i0 = 0, i1 = 0, i2 = 0, i3 = 0;   // plot: rows/tile, max degree, common degree, max res
   size_t smem = 0;                      // rowor dynamic shared memory
   uint64_t* p = nullptr;                // memset / and output
@@ -87,8 +88,13 @@ const char* op_name(const Op& op) {
     case OP_PREP: return "plot_prep_kernel";
     case OP_PLOT: return "plot_kernel";
     case OP_MEMSET: return "memset";
-    case OP_RESHAPE: return "reshape_kernel";
+    case OP_RESHAPE:
+      return op.rd.mode == kReshapeTranspose ? "reshape_transpose_kernel"
+             : op.rd.mode == kReshapeWords   ? "reshape_words_kernel"
+                                             : "reshape_kernel";
     case OP_AND: return "and_kernel";
+    case OP_OUTER: return "outer_kernel";
+    case OP_DOT: return op.nw > 16 ? "dot_wide_kernel" : "dot_kernel";
     default: return "rowor_kernel";
   }
 }
@@ -162,6 +168,98 @@ bool same_layout(const BitArr& x, const BitArr& y) {
   return small.inner >= 1 && small.rowlen() % 64 == 0;
 }
 
+// Output words per step of output axis a (a non-last inner axis needs a
+// row length that is a multiple of 64 beyond it, which the callers check).
+int64_t out_word_stride(const BitArr& out, int a) {
+  const int outer = out.ndim - out.inner;
+  int64_t st = 1;
+  if (a < outer) {
+    for (int b = a + 1; b < outer; ++b) st *= out.res[b];
+    return st * out.row_words();
+  }
+  for (int b = a + 1; b < out.ndim; ++b) st *= out.res[b];
+  return st / 64;
+}
+
+// Pick the fastest reshape kernel whose preconditions hold (strides of `d`
+// already filled in).  Words: the last output axis L is the input's last axis
+// and its runs start on word boundaries.  Transpose: L steps by input rows or
+// by whole input words, the input's last axis J is kept, both packed axes
+// start on word boundaries, nothing is reduced.
+void choose_reshape_mode(ReshapeDesc& d, const BitArr& in, const BitArr& out) {
+  d.mode = kReshapeBits;
+  d.row_any = 0;
+  if (d.nred > 0) {
+    // every packed input axis reduced: OR whole rows instead of single bits
+    bool all_inner_reduced = in.inner > 0;
+    for (int a = 0; a < out.ndim && all_inner_reduced; ++a) all_inner_reduced = d.col_stride[a] == 0;
+    if (all_inner_reduced) {
+      int n = 0;
+      for (int q = 0; q < d.nred; ++q) {
+        if (d.red_col_stride[q] != 0) continue;
+        d.red_res[n] = d.red_res[q];
+        d.red_row_stride[n] = d.red_row_stride[q];
+        d.red_col_stride[n] = 0;
+        ++n;
+      }
+      d.nred = n;
+      d.row_any = 1;
+      return;
+    }
+  }
+  if (out.ndim == 0 || out.inner == 0 || in.ndim == 0) return;
+  const int L = out.ndim - 1;
+  const int64_t R = out.res[L];
+  const bool l_aligned = (R % 64 == 0) || out.inner == 1;
+  if (!l_aligned) return;
+  if (d.col_stride[L] == 1 && (R % 64 == 0 || (in.inner == 1 && out.inner == 1))) {
+    bool ok = true;
+    for (int a = 0; a < L && ok; ++a) ok = (d.col_stride[a] % 64 == 0);
+    for (int q = 0; q < d.nred && ok; ++q) ok = (d.red_col_stride[q] % 64 == 0);
+    if (ok) {
+      d.mode = kReshapeWords;
+      d.nu = out.ndim;
+      for (int a = 0; a < L; ++a) {
+        d.u_res[a] = out.res[a];
+        d.u_in[a] = d.row_stride[a] * d.in_row_words + d.col_stride[a] / 64;
+      }
+      d.u_res[L] = (R + 63) / 64;
+      d.u_in[L] = 1;
+      for (int q = 0; q < d.nred; ++q)
+        d.red_in_w[q] = d.red_row_stride[q] * d.in_row_words + d.red_col_stride[q] / 64;
+      return;
+    }
+  }
+  if (d.nred != 0) return;
+  // L steps by whole input rows, or by whole words inside a row
+  const bool l_row = d.row_stride[L] > 0 && d.col_stride[L] == 0;
+  const bool l_col = d.row_stride[L] == 0 && d.col_stride[L] > 0 && d.col_stride[L] % 64 == 0;
+  if (!l_row && !l_col) return;
+  int J = -1;
+  for (int a = 0; a < L; ++a)
+    if (d.col_stride[a] == 1) J = a;
+  if (J < 0) return;
+  const int64_t Q = out.res[J];
+  if (!(in.inner == 1 || Q % 64 == 0)) return;
+  for (int a = 0; a < L; ++a)
+    if (a != J && d.col_stride[a] % 64 != 0) return;
+  d.mode = kReshapeTranspose;
+  d.nu = 0;
+  d.n_other = 1;
+  for (int a = 0; a < L; ++a) {
+    if (a == J) continue;
+    d.u_res[d.nu] = out.res[a];
+    d.u_in[d.nu] = d.row_stride[a] * d.in_row_words + d.col_stride[a] / 64;
+    d.u_out[d.nu] = out_word_stride(out, a);
+    d.n_other *= out.res[a];
+    d.nu++;
+  }
+  d.tQ = Q;
+  d.tR = R;
+  d.t_in_L = d.row_stride[L] * d.in_row_words + d.col_stride[L] / 64;
+  d.t_out_J = out_word_stride(out, J);
+}
+
 // out <- in with axes matched by variable; input axes missing from out are
 // OR-reduced, output axes missing from in are broadcast.
 void reshape(Builder& bd, const BitArr& in, const BitArr& out) {
@@ -198,14 +296,7 @@ void reshape(Builder& bd, const BitArr& in, const BitArr& out) {
     d.red_res[q] = in.res[ia];
     strides(ia, d.red_row_stride[q], d.red_col_stride[q]);
   }
-  // word mode: identical inner axes, nothing reduced or broadcast inside a row
-  bool wm = (out.inner == in.inner) && out.inner > 0;
-  for (int j = 0; wm && j < out.inner; ++j) {
-    const int oa = out.ndim - out.inner + j, ia = in.ndim - in.inner + j;
-    wm = (out.vars[oa] == in.vars[ia]) && (out.res[oa] == in.res[ia]);
-  }
-  for (int q = 0; wm && q < d.nred; ++q) wm = (d.red_col_stride[q] == 0);
-  d.word_mode = wm ? 1 : 0;
+  choose_reshape_mode(d, in, out);
   bd.st.n_reshapes++;
   Op op;
   op.kind = OP_RESHAPE;
@@ -278,6 +369,8 @@ void flush_rowor(Builder& bd) {
 // fewer bits need reshaping, then the wider packed side as B.
 struct JoinShape {
   bool hadamard = false;
+  bool outer = false;           // nothing summed: C[batch][M][N] = A[batch][M] AND B[batch][N]
+  bool dot = false;             // nothing kept from B alone: C[batch][M] = OR_K A AND B[batch][K]
   bool swap = false;            // A = Y, B = X
   std::vector<int> a_axes, b_axes, c_axes;
   int kinner = 0, ninner = 0;   // number of K and N axes
@@ -338,14 +431,25 @@ JoinShape analyze_join(const BitArr& X, const BitArr& Y, const std::vector<int>&
     a_axes.insert(a_axes.end(), c.K.begin(), c.K.end());
     b_axes.insert(b_axes.end(), c.K.begin(), c.K.end());
     b_axes.insert(b_axes.end(), c.N.begin(), c.N.end());
-    if (!same_layout(A, make_arr(a_axes, vres, (int)c.K.size()))) c.reshape_bits += (double)A.bits();
-    if (!same_layout(B, make_arr(b_axes, vres, (int)c.N.size()))) c.reshape_bits += (double)B.bits();
+    // a K-free cluster reads A as one flat bit vector over (batch, M); an
+    // N-free one reads B as one packed row of K bits per batch value
+    const int a_inner = c.K.empty() ? (int)a_axes.size() : (int)c.K.size();
+    const int b_inner = (c.N.empty() && !c.K.empty()) ? (int)c.K.size() : (int)c.N.size();
+    if (!same_layout(A, make_arr(a_axes, vres, a_inner))) c.reshape_bits += (double)A.bits();
+    if (!same_layout(B, make_arr(b_axes, vres, b_inner))) c.reshape_bits += (double)B.bits();
     for (int v : c.N) c.nbits *= (double)vres[v];
     return c;
   };
   Choice c0 = evaluate(false), c1 = evaluate(true);
-  js.swap = (c1.reshape_bits < c0.reshape_bits ||
-             (c1.reshape_bits == c0.reshape_bits && c1.nbits > c0.nbits));
+  js.outer = K.empty();
+  if (js.outer && (c0.N.empty() != c1.N.empty()))
+    js.swap = c0.N.empty();  // keep packed result rows: the side with N axes is B
+  else if (c1.reshape_bits != c0.reshape_bits)
+    js.swap = c1.reshape_bits < c0.reshape_bits;
+  else if (c0.N.empty() != c1.N.empty())
+    js.swap = c0.N.empty();
+  else
+    js.swap = c1.nbits > c0.nbits;
   const Choice& ch = js.swap ? c1 : c0;
   js.a_axes = js.b_axes = js.c_axes = ch.batch;
   js.a_axes.insert(js.a_axes.end(), ch.M.begin(), ch.M.end());
@@ -356,6 +460,7 @@ JoinShape analyze_join(const BitArr& X, const BitArr& Y, const std::vector<int>&
   js.c_axes.insert(js.c_axes.end(), ch.N.begin(), ch.N.end());
   js.kinner = (int)ch.K.size();
   js.ninner = (int)ch.N.size();
+  js.dot = !js.outer && ch.N.empty();
   for (int v : ch.batch) js.nbatch *= vres[v];
   for (int v : ch.M) js.M *= vres[v];
   for (int v : ch.K) js.K *= vres[v];
@@ -374,6 +479,7 @@ JoinShape analyze_join(const BitArr& X, const BitArr& Y, const std::vector<int>&
 BitArr join_result_layout(const JoinShape& js, const std::vector<int>& keep,
                           const std::vector<int64_t>& vres) {
   if (js.hadamard) return make_arr(keep, vres, keep.empty() ? 0 : 1);
+  if (js.dot) return make_arr(js.c_axes, vres, (int)js.c_axes.size());
   return make_arr(js.c_axes, vres, js.ninner);
 }
 
@@ -407,6 +513,42 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
 
   const BitArr& A = js.swap ? Y : X;
   const BitArr& B = js.swap ? X : Y;
+  if (js.outer) {
+    BitArr Am = conform(bd, A, make_arr(js.a_axes, vres, (int)js.a_axes.size()));
+    BitArr Bm = conform(bd, B, make_arr(js.b_axes, vres, js.ninner));
+    BitArr C = make_arr(js.c_axes, vres, js.ninner);
+    if (target && target->w && same_layout(C, *target)) C.w = target->w;
+    else C.w = bd.alloc_words(C.words());
+    Op op;
+    op.kind = OP_OUTER;
+    op.a = Am.w;
+    op.b = Bm.w;
+    op.p = C.w;
+    op.count = js.nbatch * js.M;
+    op.m = js.M;
+    op.nw = Bm.row_words();
+    bd.ops.push_back(op);
+    bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
+    return C;
+  }
+  if (js.dot) {
+    BitArr Am = conform(bd, A, make_arr(js.a_axes, vres, js.kinner));
+    BitArr Bm = conform(bd, B, make_arr(js.b_axes, vres, js.kinner));
+    BitArr C = make_arr(js.c_axes, vres, (int)js.c_axes.size());
+    if (target && target->w && same_layout(C, *target)) C.w = target->w;
+    else C.w = bd.alloc_words(C.words());
+    Op op;
+    op.kind = OP_DOT;
+    op.a = Am.w;
+    op.b = Bm.w;
+    op.p = C.w;
+    op.count = js.nbatch * js.M;
+    op.m = js.M;
+    op.nw = Am.row_words();
+    bd.ops.push_back(op);
+    bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
+    return C;
+  }
   BitArr Am = conform(bd, A, make_arr(js.a_axes, vres, js.kinner));
   BitArr Bm = conform(bd, B, make_arr(js.b_axes, vres, js.ninner));
   BitArr C = make_arr(js.c_axes, vres, js.ninner);
@@ -746,6 +888,12 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
         break;
       case OP_AND:
         launch_and(op.a, op.b, op.p, op.count, s);
+        break;
+      case OP_OUTER:
+        launch_outer(op.a, op.b, op.p, op.count, op.m, op.nw, s);
+        break;
+      case OP_DOT:
+        launch_dot(op.a, op.b, op.p, op.count, op.m, op.nw, s);
         break;
       case OP_ROWOR:
         check_cuda(ctx,

@@ -17,13 +17,20 @@
 namespace pa {
 
 // --------------------------------------------------------------- reshape
+// Bit mode: one warp per output word, one lane per bit (two ballots pack the
+// 64 bits).  Every bit is decoded and gathered on its own, OR-ed over the
+// reduced axes with an early exit.  With row_any set, every packed input axis
+// is reduced and red_* hold only the reduced row axes: a bit is then the OR of
+// whole input rows, scanned by words (padding bits are zero).
 __global__ void reshape_kernel(const ReshapeDesc d) {
+  const int lane = threadIdx.x & 31;
   const int64_t total = d.out_nrows * d.out_row_words;
   const int outer = d.out_ndim - d.out_inner;
   int64_t red_total = 1;
   for (int q = 0; q < d.nred; ++q) red_total *= d.red_res[q];
-  for (int64_t ow = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ow < total;
-       ow += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t ow = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ow < total;
+       ow += nwarps) {
     const int64_t orow = ow / d.out_row_words, w = ow % d.out_row_words;
     int64_t brow = 0, bcol = 0, rest = orow;
     for (int a = outer - 1; a >= 0; --a) {
@@ -32,24 +39,12 @@ __global__ void reshape_kernel(const ReshapeDesc d) {
       brow += v * d.row_stride[a];
       bcol += v * d.col_stride[a];
     }
-    uint64_t word = 0;
-    if (d.word_mode) {
-      // columns map 1:1: OR whole input words over the reduced axes
-      int64_t cnt[2 * kMaxDim] = {};
-      int64_t rr = brow;
-      for (int64_t s = 0; s < red_total; ++s) {
-        word |= d.in[rr * d.in_row_words + w];
-        for (int q = d.nred - 1; q >= 0; --q) {
-          rr += d.red_row_stride[q];
-          if (++cnt[q] < d.red_res[q]) break;
-          rr -= d.red_row_stride[q] * d.red_res[q];
-          cnt[q] = 0;
-        }
-      }
-    } else {
-      for (int b = 0; b < 64; ++b) {
-        const int64_t ocol = w * 64 + b;
-        if (ocol >= d.out_rowlen) break;
+    uint32_t half[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t ocol = w * 64 + h * 32 + lane;
+      bool bit = false;
+      if (ocol < d.out_rowlen) {
         int64_t rr = brow, cc = bcol, rest2 = ocol;
         for (int a = d.out_ndim - 1; a >= outer; --a) {
           const int64_t v = rest2 % d.out_res[a];
@@ -58,9 +53,15 @@ __global__ void reshape_kernel(const ReshapeDesc d) {
           cc += v * d.col_stride[a];
         }
         int64_t cnt[2 * kMaxDim] = {};
-        uint64_t bit = 0;
         for (int64_t s = 0; s < red_total && !bit; ++s) {
-          bit = (d.in[rr * d.in_row_words + (cc >> 6)] >> (cc & 63)) & 1ull;
+          if (d.row_any) {
+            const uint64_t* row = d.in + rr * d.in_row_words;
+            uint64_t acc = 0;
+            for (int64_t k = 0; k < d.in_row_words && !acc; ++k) acc = row[k];
+            bit = acc != 0;
+          } else {
+            bit = (d.in[rr * d.in_row_words + (cc >> 6)] >> (cc & 63)) & 1ull;
+          }
           for (int q = d.nred - 1; q >= 0; --q) {
             rr += d.red_row_stride[q];
             cc += d.red_col_stride[q];
@@ -70,19 +71,239 @@ __global__ void reshape_kernel(const ReshapeDesc d) {
             cnt[q] = 0;
           }
         }
-        word |= bit << b;
+      }
+      half[h] = __ballot_sync(0xffffffffu, bit);
+    }
+    if (lane == 0) d.out[ow] = (uint64_t)half[0] | ((uint64_t)half[1] << 32);
+  }
+}
+
+// Words mode: output word index -> input word index through the mixed-radix
+// decomposition (u_res, u_in), then an OR over the reduced axes.  Index type I
+// is 32-bit when every word index fits.
+template <class I>
+__global__ void reshape_words_kernel(const ReshapeDesc d) {
+  const I total = (I)(d.out_nrows * d.out_row_words);
+  I red_total = 1;
+  for (int q = 0; q < d.nred; ++q) red_total *= (I)d.red_res[q];
+  for (I ow = (I)blockIdx.x * blockDim.x + threadIdx.x; ow < total; ow += (I)gridDim.x * blockDim.x) {
+    I rest = ow, src = 0;
+    for (int a = d.nu - 1; a >= 0; --a) {
+      const I r = (I)d.u_res[a];
+      const I q = rest / r;
+      src += (rest - q * r) * (I)d.u_in[a];
+      rest = q;
+    }
+    uint64_t word = 0;
+    I cnt[2 * kMaxDim] = {};
+    for (I s = 0; s < red_total; ++s) {
+      word |= d.in[src];
+      for (int q = d.nred - 1; q >= 0; --q) {
+        src += (I)d.red_in_w[q];
+        if (++cnt[q] < (I)d.red_res[q]) break;
+        src -= (I)d.red_in_w[q] * (I)d.red_res[q];
+        cnt[q] = 0;
       }
     }
     d.out[ow] = word;
   }
 }
 
+// In-register transpose of a 64 x 64 bit block held by one warp: lane l holds
+// rows l (lo) and l + 32 (hi), bit c of a row being column c.  Afterwards lane l
+// holds columns l and l + 32 as rows.  Recursive block swap (halves, quarters,
+// ... single bits): for block size s the rows r and r + s (r & s == 0) exchange
+// the columns c + s of row r with the columns c of row r + s (c & s == 0).
+__device__ __forceinline__ void transpose64(uint64_t& lo, uint64_t& hi, int lane) {
+  uint64_t t = ((lo >> 32) ^ hi) & 0x00000000FFFFFFFFull;
+  hi ^= t;
+  lo ^= t << 32;
+  const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                             0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int s = 16 >> i;
+    const uint64_t m = masks[i];
+    const uint64_t plo = __shfl_xor_sync(0xffffffffu, lo, s);
+    const uint64_t phi = __shfl_xor_sync(0xffffffffu, hi, s);
+    if (lane & s) {
+      lo ^= ((plo >> s) ^ lo) & m;
+      hi ^= ((phi >> s) ^ hi) & m;
+    } else {
+      lo ^= (((lo >> s) ^ plo) & m) << s;
+      hi ^= (((hi >> s) ^ phi) & m) << s;
+    }
+  }
+}
+
+// Transpose mode.  A CTA tile is 256 values of L (4 output words) x 256 values
+// of J (4 input words) at one value of the other axes: coalesced 32-byte loads
+// of 256 input rows into shared memory, 16 warp transposes of 64 x 64 blocks,
+// coalesced 32-byte stores of 256 output rows.  Rows of the shared tiles are
+// padded to 5 words so the column reads of a block are free of bank conflicts.
+constexpr int kTrPad = 5;
+__global__ void __launch_bounds__(256) reshape_transpose_kernel(const ReshapeDesc d) {
+  __shared__ uint64_t s_in[256 * kTrPad];
+  __shared__ uint64_t s_out[256 * kTrPad];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nJT = (d.tQ + 255) / 256, nLT = (d.tR + 255) / 256;
+  const int64_t tiles = d.n_other * nJT * nLT;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t lt = tile % nLT, r = tile / nLT, jt = r % nJT;
+    int64_t rest = r / nJT, base_in = 0, base_out = 0;
+    for (int a = d.nu - 1; a >= 0; --a) {
+      const int64_t v = rest % d.u_res[a];
+      rest /= d.u_res[a];
+      base_in += v * d.u_in[a];
+      base_out += v * d.u_out[a];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + 256 * i, b = idx >> 2, c = idx & 3;
+      const int64_t L = lt * 256 + b, jb = jt * 4 + c;
+      uint64_t v = 0;
+      if (L < d.tR && jb * 64 < d.tQ) v = d.in[base_in + L * d.t_in_L + jb];
+      s_in[b * kTrPad + c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int k = warp * 2 + i, cw = k >> 2, lw = k & 3;
+      if ((jt * 4 + cw) * 64 < d.tQ && lt * 256 + lw * 64 < d.tR) {
+        uint64_t lo = s_in[(lw * 64 + lane) * kTrPad + cw];
+        uint64_t hi = s_in[(lw * 64 + lane + 32) * kTrPad + cw];
+        transpose64(lo, hi, lane);
+        s_out[(cw * 64 + lane) * kTrPad + lw] = lo;
+        s_out[(cw * 64 + lane + 32) * kTrPad + lw] = hi;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + 256 * i, t = idx >> 2, w = idx & 3;
+      const int64_t J = jt * 256 + t, lw = lt * 4 + w;
+      if (J < d.tQ && lw * 64 < d.tR) d.out[base_out + J * d.t_out_J + lw] = s_out[t * kTrPad + w];
+    }
+    __syncthreads();
+  }
+}
+
 void launch_reshape(const ReshapeDesc& d, cudaStream_t s) {
   const int64_t total = d.out_nrows * d.out_row_words;
   if (total <= 0) return;
+  if (d.mode == kReshapeTranspose) {
+    const int64_t tiles = d.n_other * ((d.tQ + 255) / 256) * ((d.tR + 255) / 256);
+    reshape_transpose_kernel<<<(unsigned)std::min<int64_t>(tiles, 152 * 8), 256, 0, s>>>(d);
+    return;
+  }
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (d.mode == kReshapeWords) {
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    int64_t in_max = 0;  // largest input word index + 1 (bounded by the sum below)
+    for (int a = 0; a < d.nu; ++a) in_max += (d.u_res[a] - 1) * d.u_in[a];
+    for (int q = 0; q < d.nred; ++q) in_max += (d.red_res[q] - 1) * d.red_in_w[q];
+    if (total + 256 * blocks < (1ll << 31) && in_max < (1ll << 31))
+      reshape_words_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(d);
+    else
+      reshape_words_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(d);
+    return;
+  }
+  blocks = (total + 7) / 8;  // one warp per word
+  if (blocks > 152 * 16) blocks = 152 * 16;
   reshape_kernel<<<(unsigned)blocks, 256, 0, s>>>(d);
+}
+
+// ----------------------------------------------------------------- outer
+// C[r][w] = bit r of A ? B[r / M][w] : 0, one thread per output word.
+template <class I>
+__global__ void outer_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                             uint64_t* __restrict__ C, I rows, I M, I Nw) {
+  const I total = rows * Nw;
+  for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (I)gridDim.x * blockDim.x) {
+    const I r = i / Nw, w = i - r * Nw;
+    const uint64_t bit = (A[r >> 6] >> (r & 63)) & 1ull;
+    C[i] = bit ? B[(r / M) * Nw + w] : 0ull;
+  }
+}
+
+void launch_outer(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
+                  int64_t Nw, cudaStream_t s) {
+  const int64_t total = rows * Nw;
+  if (total <= 0) return;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (total + 256 * blocks < (1ll << 31))
+    outer_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(A, B, C, (uint32_t)rows, (uint32_t)M,
+                                                             (uint32_t)Nw);
+  else
+    outer_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(A, B, C, rows, M, Nw);
+}
+
+// ------------------------------------------------------------------- dot
+// One warp per 64-bit word of C: lanes take bits r and r + 32, AND their A
+// row with the batch's B row word by word, and two ballots pack the bits.
+__global__ void dot_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                           uint64_t* __restrict__ C, int64_t rows, int64_t M, int64_t Kw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t words = (rows + 63) / 64;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t cw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cw < words;
+       cw += nwarps) {
+    uint32_t half[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t r = cw * 64 + h * 32 + lane;
+      uint64_t acc = 0;
+      if (r < rows) {
+        const uint64_t* a = A + r * Kw;
+        const uint64_t* b = B + (r / M) * Kw;
+        for (int64_t w = 0; w < Kw && !acc; ++w) acc = a[w] & b[w];
+      }
+      half[h] = __ballot_sync(0xffffffffu, acc != 0);
+    }
+    if (lane == 0) C[cw] = (uint64_t)half[0] | ((uint64_t)half[1] << 32);
+  }
+}
+
+// Long rows (more than 16 words): one warp per (row, run of 256 words), lanes
+// on consecutive words; a row whose run meets a common bit sets its bit of the
+// pre-zeroed C atomically.
+constexpr int64_t kDotRun = 256;
+__global__ void dot_wide_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                                unsigned long long* __restrict__ C, int64_t rows, int64_t M,
+                                int64_t Kw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nruns = (Kw + kDotRun - 1) / kDotRun;
+  const int64_t items = rows * nruns;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
+       it += nwarps) {
+    const int64_t r = it / nruns, w0 = (it - r * nruns) * kDotRun;
+    const int64_t w1 = min(Kw, w0 + kDotRun);
+    const uint64_t* a = A + r * Kw;
+    const uint64_t* b = B + (r / M) * Kw;
+    uint64_t acc = 0;
+    for (int64_t w = w0 + lane; w < w1; w += 32) acc |= a[w] & b[w];
+    if (__any_sync(0xffffffffu, acc != 0) && lane == 0) atomicOr(&C[r >> 6], 1ull << (r & 63));
+  }
+}
+
+void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
+                int64_t Kw, cudaStream_t s) {
+  const int64_t words = (rows + 63) / 64;
+  if (words <= 0) return;
+  if (Kw > 16) {
+    cudaMemsetAsync(C, 0, (size_t)words * 8, s);
+    const int64_t items = rows * ((Kw + kDotRun - 1) / kDotRun);
+    int64_t blocks = (items + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    dot_wide_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, reinterpret_cast<unsigned long long*>(C),
+                                                     rows, M, Kw);
+    return;
+  }
+  int64_t blocks = (words + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, C, rows, M, Kw);
 }
 
 // ---------------------------------------------------------------- row-OR

@@ -86,9 +86,20 @@ struct BitArr {
   int64_t bits() const { return nrows() * rowlen(); }
 };
 
+// Reshape modes (contract.cu):
+//  kReshapeBits       any mapping; every output bit gathered on its own
+//  kReshapeWords      the last output axis runs along input words: every output
+//                     word is one input word (OR-ed over reduced axes), found
+//                     through word strides u_in over the output-word axes u_res
+//  kReshapeTranspose  the last output axis L steps by input rows or whole
+//                     input words and the input's last axis J is kept: 64 x 64
+//                     bit blocks are transposed; u_res / u_in / u_out cover
+//                     the other axes
+enum { kReshapeBits = 0, kReshapeWords = 1, kReshapeTranspose = 2 };
+
 // General gather: out bit (axes of `out`) = OR over the reduced input axes of
-// the input bit with the same values of the shared axes.  out_from_in[a] is the
-// input axis feeding output axis a (-1: broadcast along a).
+// the input bit with the same values of the shared axes.  An output axis that
+// is missing from the input has zero strides (broadcast).
 struct ReshapeDesc {
   const uint64_t* in;
   uint64_t* out;
@@ -102,9 +113,28 @@ struct ReshapeDesc {
   int64_t red_row_stride[2 * kMaxDim];
   int64_t red_col_stride[2 * kMaxDim];
   int64_t in_row_words;
-  int32_t word_mode;  // 1: output columns map 1:1 onto input columns (copy words)
+  int32_t mode;                      // kReshape*
+  int32_t row_any;                   // bit mode: all packed input axes reduced (see contract.cu)
+  int32_t nu;                        // axes of the word / tile decomposition
+  int64_t u_res[2 * kMaxDim];
+  int64_t u_in[2 * kMaxDim];         // input words per step of the axis
+  int64_t u_out[2 * kMaxDim];        // output words per step (transpose mode)
+  int64_t red_in_w[2 * kMaxDim];     // words mode: input words per reduced step
+  int64_t tQ, tR;                    // transpose: resolutions of J and L
+  int64_t t_in_L, t_out_J;           // input words per L step, output words per J step
+  int64_t n_other;                   // transpose: product of u_res
 };
 void launch_reshape(const ReshapeDesc& d, cudaStream_t s);
+
+// Outer product of a K-free cluster: C row r (r = b * M + m) is B row b when bit
+// r of the flat bit vector A is set, else zero.  rows = nbatch * M.
+void launch_outer(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
+                  int64_t Nw, cudaStream_t s);
+// Cluster whose result keeps no axis of B alone: bit r (r = b * M + m) of the
+// flat bit vector C is set when row r of A and row b of B (Kw words each)
+// share a set bit.  rows = nbatch * M.
+void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
+                int64_t Kw, cudaStream_t s);
 
 // C[b*M + m, :] |= B[b*K + k, :] for every set bit k of A[b*M + m, :].
 // One CTA owns a tile of B (Kc rows x Nt words of batch b) in shared memory and
