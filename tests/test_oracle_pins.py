@@ -426,6 +426,21 @@ def test_mlp_oracle_forward_by_hand():
     assert y.tolist() == [0.5, 3.5, 9.5]
 
 
+def test_mlp_oracle_adam_first_steps():
+    """Adam from zero moments: the bias corrections make the first step
+    lr * g / (|g| + eps), i.e. lr * sign(g) for |g| >> eps; a constant gradient
+    keeps that step size on later steps; a zero gradient does not move."""
+    from oracle import mlp as M
+    g = np.array([3.0, -0.5, 1e-3, 0.0])
+    p0 = np.array([1.0, 2.0, -1.0, 0.25])
+    z = np.zeros(4)
+    p1, m1, v1 = M.adam_step(p0, g, z, z, 1, 0.01)
+    assert np.allclose(p1[:3], p0[:3] - 0.01 * np.sign(g[:3]), rtol=0, atol=1e-7)
+    assert p1[3] == p0[3]
+    p2, _, _ = M.adam_step(p1, g, m1, v1, 2, 0.01)
+    assert np.allclose(p2[:3] - p1[:3], -0.01 * np.sign(g[:3]), rtol=0, atol=1e-7)
+
+
 def test_solve_strategies_agree():
     """Smallest-result pairwise joining and left-to-right folding give the same
     array (associativity), on a tree-like random network."""
