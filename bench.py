@@ -166,6 +166,10 @@ SMEM_GBS = 152 * 32 * 4 * 2070e6 / 1e9   # 152 SMs x 32 banks x 4 B x 2070 MHz
 FP32_TFLOPS = 2.0 * 152 * 128 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
+def fp8_tflops():
+    return 2.0 * (load_peaks().get("bf16_tflops") or 1900.0)
+
+
 def kernel_rooflines(kernels, stats_step, steps, sysm):
     """Roofline of every kernel with a defined algorithmic work, largest share first."""
     out = []
@@ -184,6 +188,17 @@ def kernel_rooflines(kernels, stats_step, steps, sysm):
                         "unit": "GB/s", "frac": ach / SMEM_GBS, "traffic": None,
                         "limit": "shared-memory word loads (LSU), 152 SMs x 128 B/clk x 2070 MHz, derived",
                         "work_per_launch": f"{words / launches:.4g} words OR-ed",
+                        "share": ms / total})
+        elif name == "mma_bool_kernel":
+            # 2 flops per multiply-add of the unpadded clusters (M x N x K each)
+            macs = stats_step.get("mma_macs", 0.0) * steps / launches
+            ach = 2.0 * macs / t / 1e12
+            peak = fp8_tflops()
+            out.append({"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak,
+                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                        "limit": "dense FP8 tensor rate: measured bf16 burst x 2 (nominal "
+                                 "FP8/BF16 ratio), MEASURED_PEAKS.json",
+                        "work_per_launch": f"{macs:.4g} multiply-adds",
                         "share": ms / total})
         elif name == "plot_kernel":
             # algorithmic work per pixel: the row polynomial sum_j g_j y^j, D FMAs
@@ -237,6 +252,7 @@ def run_batched(eng, pa, W, dev, reps=5):
             "batched_ms": graph_s * 1e3, "plain_systems_per_s": len(systems) / plain_s,
             "plain_ms": plain_s * 1e3, "speedup": plain_s / graph_s,
             "graph_launches": st["n_launches"], "joins": st["n_joins"],
+            "tensor_core_joins": int(st["n_mma"]),
             "pixel_ops_dense": st["pixel_ops_dense"],
             "batched_gpixel_ops_per_s": st["pixel_ops_dense"] / graph_s / 1e9,
             "plan_and_capture_s": plan_s, "workspace_bytes": st["workspace_bytes"],
@@ -308,6 +324,8 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
             "batched_learned_systems_per_s": len(nets) / l_s,
             "learned_vs_plain": plain_s / l_s, "learned_vs_batched_greedy": g_s / l_s,
             "learned_orders_kept": int(sum(learned_flags)),
+            "tensor_core_joins_greedy": int(g_st["n_mma"]),
+            "tensor_core_joins_learned": int(l_st["n_mma"]),
             "pixel_ops_dense_greedy": g_st["pixel_ops_dense"],
             "pixel_ops_dense_learned": l_st["pixel_ops_dense"],
             "timing": "batched: CUDA events around graph replays; plain: host clock, synchronised"}
@@ -321,7 +339,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = local_rank
     eng = pa.Engine(dev)
+    # the autotuner measures both contraction paths on this GPU; the automatic
+    # path choice then weighs each cluster with those rates
+    rates = eng.autotune()
+    eng.set_path(args.path)
     sysm = W.chain(res=2048, nrel=8, seed=W.SEED_BASE + 2 + rank)
+    # one logged solve measures the densities of this system's intermediates,
+    # which the automatic path choice then prefers to its independence estimate
+    _, _, observed, _ = eng.log_joins(sysm)
+    eng.sync()
     out = pa.BitArray.empty(sysm.exposed, [sysm.axes[v][2] for v in sysm.exposed], dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
@@ -388,12 +414,15 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write)",
-                   "pixel_ops_per_step": ops, "parallelism": f"independent systems x{world}"},
+                   "pixel_ops_per_step": ops, "parallelism": f"independent systems x{world}",
+                   "contract_path": args.path, "tensor_core_joins": int(st["n_mma"]),
+                   "autotuned_rates": rates,
+                   "observed_join_densities": [round(float(x), 5) for x in observed]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(out.words.numel() * 8)},
         "gpu_launches": int(st["n_launches"]) * args.steps,
         "peaks": {"hbm_gbs": load_peaks().get("hbm_gbs"), "smem_gbs_derived": SMEM_GBS,
-                  "fp32_tflops_derived": FP32_TFLOPS},
+                  "fp32_tflops_derived": FP32_TFLOPS, "fp8_tflops_derived": fp8_tflops()},
         "clocks": clk,
         "roofline": (rl[0] if rl else None),
         "roofline_other": rl[1:],
@@ -418,6 +447,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--path", default="auto", choices=["auto", "rowor", "mma"],
+                    help="contraction path of matrix-form clusters")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -144,6 +144,9 @@ typedef struct {
   int32_t n_launches;        /* kernels and memsets enqueued by the call */
   int64_t peak_words;        /* largest intermediate array, words */
   int64_t workspace_bytes;   /* workspace in use by the call */
+  double mma_macs;           /* multiply-adds of the clusters contracted on the
+                                tensor cores: sum of nbatch * M * N * K */
+  int32_t n_mma;             /* clusters contracted on the tensor cores */
 } pa_stats;
 
 /* One independent system for the batched entry points: its own variables,
@@ -182,6 +185,33 @@ pa_status pa_sync(pa_ctx* ctx, void* stream);
 pa_status pa_profile_enable(pa_ctx* ctx, int32_t on);
 pa_status pa_profile_read(pa_ctx* ctx, int32_t max_kernels, char* names, int64_t* launches,
                           double* total_ms, int32_t* nkernels);
+
+/* How a matrix-form cluster (Sec. 3.5) is contracted.  Both give the same
+ * bits.  PA_PATH_ROWOR: bit-packed row-OR on the CUDA cores (work follows the
+ * set bits of A).  PA_PATH_MMA: 0/1 E4M3 matrix product on the tensor cores
+ * (tcgen05, FP32 accumulation, thresholded at > 0; work follows M x N x K;
+ * both operands are first expanded once into E4M3 byte arrays in the
+ * workspace, (M + N) x K bytes per batch entry).
+ * PA_PATH_AUTO (default): per cluster, the faster by the context's rates and
+ * the operands' estimated densities. */
+typedef enum { PA_PATH_AUTO = 0, PA_PATH_ROWOR = 1, PA_PATH_MMA = 2 } pa_path;
+pa_status pa_set_contract_path(pa_ctx* ctx, int32_t path);
+
+/* The rates PA_PATH_AUTO compares.  Defaults were measured on a GB300;
+ * pa_autotune re-measures them on this context's GPU (a 2048 x 2048 x 2048
+ * contraction of random operands through each path, five runs timed with CUDA
+ * events on `stream` after one warm-up run) and keeps them for later calls.
+ * The row-OR rate depends on the density of A and is measured at 2 % and 16 %
+ * (log-linear in between); the tensor-core rate includes the expansion of both
+ * operands.  Blocks the host; allocates and frees about 10 MB of device memory. */
+typedef struct {
+  double rowor_words_per_us;        /* 64-bit words OR-ed by the row-OR kernel, A 2 % dense */
+  double rowor_words_per_us_dense;  /* the same, A 16 % dense */
+  double mma_macs_per_us;           /* multiply-adds of the tensor-core path */
+} pa_rates;
+pa_status pa_autotune(pa_ctx* ctx, pa_rates* out, void* stream);
+pa_status pa_get_rates(const pa_ctx* ctx, pa_rates* out);
+pa_status pa_set_rates(pa_ctx* ctx, const pa_rates* rates);
 
 /* Number of uint64 words of a pa_array of this shape (host only, no GPU). */
 int64_t pa_array_words(int32_t ndim, const int32_t* res);

@@ -19,7 +19,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native
-from ._native import PaArray, PaAxis, PaOptions, PaRelation, PaStats, PaSystem
+from ._native import PaArray, PaAxis, PaOptions, PaRates, PaRelation, PaStats, PaSystem
 
 PA_OK = 0
 STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
@@ -332,6 +332,33 @@ def pa_sync(ctx, stream=None):
     _check(_lib().pa_sync(ctx, _stream_ptr(stream)), ctx)
 
 
+PATHS = {"auto": 0, "rowor": 1, "mma": 2}
+
+
+def pa_set_contract_path(ctx, path="auto"):
+    """How matrix-form clusters are contracted: "auto", "rowor" or "mma"."""
+    _check(_lib().pa_set_contract_path(ctx, PATHS[path] if isinstance(path, str) else int(path)),
+           ctx)
+
+
+def pa_autotune(ctx, stream=None) -> dict:
+    """Measure the row-OR, tensor-core and expansion rates on this GPU; returns them."""
+    r = PaRates()
+    _check(_lib().pa_autotune(ctx, ctypes.byref(r), _stream_ptr(stream)), ctx)
+    return r.as_dict()
+
+
+def pa_get_rates(ctx) -> dict:
+    r = PaRates()
+    _check(_lib().pa_get_rates(ctx, ctypes.byref(r)), ctx)
+    return r.as_dict()
+
+
+def pa_set_rates(ctx, rates: dict):
+    r = PaRates(**{k: float(v) for k, v in rates.items()})
+    _check(_lib().pa_set_rates(ctx, ctypes.byref(r)), ctx)
+
+
 # ------------------------------------------------------------------ Engine
 class Engine:
     """One context on one GPU; allocates outputs as torch tensors."""
@@ -339,6 +366,12 @@ class Engine:
     def __init__(self, device: int = 0, workspace_cap: int = 0):
         self.device = device
         self.ctx = pa_create(device, workspace_cap)
+
+    def set_path(self, path="auto"):
+        pa_set_contract_path(self.ctx, path)
+
+    def autotune(self, stream=None) -> dict:
+        return pa_autotune(self.ctx, stream)
 
     def close(self):
         if self.ctx:

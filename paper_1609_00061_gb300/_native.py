@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
 _ROOT = os.path.dirname(_HERE)
 INCLUDE = os.path.join(_ROOT, "include")
 
-CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu"]
+CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu", "mma.cu"]
 CPP_SOURCES = ["planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -95,7 +95,15 @@ class PaStats(ctypes.Structure):
     _fields_ = [("pixels_plotted", c_f64), ("pixel_ops_dense", c_f64),
                 ("words_or_executed", c_f64), ("n_plots", c_i32), ("n_joins", c_i32),
                 ("n_reshapes", c_i32), ("n_launches", c_i32), ("peak_words", c_i64),
-                ("workspace_bytes", c_i64)]
+                ("workspace_bytes", c_i64), ("mma_macs", c_f64), ("n_mma", c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PaRates(ctypes.Structure):
+    _fields_ = [("rowor_words_per_us", c_f64), ("rowor_words_per_us_dense", c_f64),
+                ("mma_macs_per_us", c_f64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,7 +122,8 @@ EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_word
            "pa_solve_network_static", "pa_plan_order", "pa_tree_cost",
            "pa_mlp_create", "pa_mlp_destroy", "pa_mlp_num_params", "pa_mlp_get_params",
            "pa_mlp_set_params", "pa_mlp_get_grads", "pa_mlp_forward", "pa_mlp_backward",
-           "pa_mlp_adam", "pa_join_log", "pa_plan_learned"]
+           "pa_mlp_adam", "pa_join_log", "pa_plan_learned",
+           "pa_set_contract_path", "pa_autotune", "pa_get_rates", "pa_set_rates"]
 
 _lib = None
 
@@ -194,5 +203,13 @@ def load(build_if_missing: bool = True):
     lib.pa_tree_cost.argtypes = [c_i32, P(c_f64), c_i32, P(c_i32), P(c_i32), c_i32, P(c_i32),
                                  c_i32, P(c_i32), P(c_i32), P(c_f64), P(c_f64)]
     lib.pa_tree_cost.restype = c_i32
+    lib.pa_set_contract_path.argtypes = [vp, c_i32]
+    lib.pa_set_contract_path.restype = c_i32
+    lib.pa_autotune.argtypes = [vp, P(PaRates), vp]
+    lib.pa_autotune.restype = c_i32
+    lib.pa_get_rates.argtypes = [vp, P(PaRates)]
+    lib.pa_get_rates.restype = c_i32
+    lib.pa_set_rates.argtypes = [vp, P(PaRates)]
+    lib.pa_set_rates.restype = c_i32
     _lib = lib
     return lib

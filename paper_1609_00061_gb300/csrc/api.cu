@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "mlp.h"
@@ -42,6 +43,14 @@ struct pa_ctx {
   };
   std::vector<Rec> recs;
   size_t ev_used = 0;
+  // contraction path (pa_set_contract_path) and the rates its automatic
+  // choice compares (defaults measured on a GB300; pa_autotune re-measures)
+  int path = PA_PATH_AUTO;
+  double rate_or = 2.0e5;      // row-OR: B words OR-ed per microsecond, A 2 % dense
+  double rate_or_dense = 9.0e5;  // the same, A 16 % dense
+  double rate_mma = 4.4e8;     // tensor path (with operand expansion): multiply-adds per microsecond
+  std::unordered_map<uint64_t, double> dens_cache;  // relation key -> estimated plot density
+  std::unordered_map<uint64_t, double> obs_dens;    // subtree key -> density measured by pa_join_log
 };
 
 namespace pa {
@@ -66,14 +75,15 @@ pa_status set_err(pa_ctx* ctx, pa_status st, const std::string& msg) {
 bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
 // ------------------------------------------------------------ program
-enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT };
+enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
+              OP_MMA };
 
 struct Op {
   OpKind kind;
   size_t off0 = 0, off1 = 0, off2 = 0;  // blob offsets (plot jobs; rowor descs, maps, cta0)
   int n = 0;                            // plot jobs / rowor problems
   int64_t count = 0;                    // prep items / plot tiles / rowor grid / words / rows
-  int64_t m = 0, nw = 0;                // outer: M and words per row
+  int64_t m = 0, nw = 0;                // outer / dot: M and words per row
   int i0 = 0, i1 = 0, i2 = 0, i3 = 0;   // plot: rows/tile, max degree, common degree, max res
   size_t smem = 0;                      // rowor dynamic shared memory
   uint64_t* p = nullptr;                // memset / and output
@@ -95,6 +105,8 @@ const char* op_name(const Op& op) {
     case OP_AND: return "and_kernel";
     case OP_OUTER: return "outer_kernel";
     case OP_DOT: return op.nw > 16 ? "dot_wide_kernel" : "dot_kernel";
+    case OP_UNPACK: return "unpack_kernels";
+    case OP_MMA: return "mma_bool_kernel";
     default: return "rowor_kernel";
   }
 }
@@ -112,6 +124,7 @@ struct Builder {
   int* d_err = nullptr;
   unsigned long long* d_stat = nullptr;
   std::vector<RowOrDesc> pend;  // contractions waiting for one shared launch
+  std::vector<MmaDesc> pend_mma;  // tensor-core contractions waiting for one launch
 
   Builder(pa_ctx* c, bool dry_, char* base_, size_t blob_cap_)
       : ctx(c), dry(dry_), base(base_), used(blob_cap_), blob_cap(blob_cap_) {}
@@ -327,8 +340,52 @@ BitArr make_arr(const std::vector<int>& vars, const std::vector<int64_t>& vres, 
   return a;
 }
 
-// The waiting contractions as launches: one per tile width.
+// The waiting tensor-core contractions as one launch.
+void flush_mma(Builder& bd) {
+  if (bd.pend_mma.empty()) return;
+  const size_t n = bd.pend_mma.size();
+  std::vector<CUtensorMap> maps(2 * n);
+  std::vector<int64_t> cta0(n + 1, 0);
+  for (size_t p = 0; p < n; ++p) {
+    if (bd.dry) memset(&maps[2 * p], 0, 2 * sizeof(CUtensorMap));
+    else if (mma_encode_maps(bd.pend_mma[p], &maps[2 * p]) != cudaSuccess)
+      bd.fail(PA_ERR_CUDA, "cuTensorMapEncodeTiled failed (tensor-core path)");
+    cta0[p + 1] = cta0[p] + mma_ctas(bd.pend_mma[p]);
+  }
+  // one launch per operand kind expands every problem's operands, then one
+  // launch contracts them all
+  Op up;
+  up.kind = OP_UNPACK;
+  up.off0 = bd.put(bd.pend_mma.data(), n, 64);
+  up.n = (int)n;
+  for (const MmaDesc& d : bd.pend_mma) {
+    up.m = std::max<int64_t>(up.m, unpack_blocks_a(d));
+    up.nw = std::max<int64_t>(up.nw, unpack_blocks_b(d));
+  }
+  if (n > 65535) bd.fail(PA_ERR_TOO_LARGE, "more than 65535 tensor-core problems in one level");
+  bd.ops.push_back(up);
+  Op op;
+  op.kind = OP_MMA;
+  op.off0 = up.off0;
+  op.off1 = bd.put(maps.data(), maps.size(), 128);
+  op.off2 = bd.put(cta0.data(), cta0.size(), 16);
+  op.n = (int)n;
+  op.count = cta0.back();
+  if (op.count > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "contraction grid too large");
+  bd.ops.push_back(op);
+  bd.pend_mma.clear();
+}
+
+void flush_rowor_only(Builder& bd);
+
+// The waiting contractions as launches: one per tile width, one for the
+// tensor-core path.
 void flush_rowor(Builder& bd) {
+  flush_rowor_only(bd);
+  flush_mma(bd);
+}
+
+void flush_rowor_only(Builder& bd) {
   std::vector<int> done(bd.pend.size(), 0);
   for (size_t i = 0; i < bd.pend.size(); ++i) {
     if (done[i]) continue;
@@ -486,11 +543,49 @@ BitArr join_result_layout(const JoinShape& js, const std::vector<int>& keep,
 // One two-array cluster.  When `target` is given and the result lands in its
 // layout, the result is written there.  Row-OR contractions wait in bd.pend
 // for flush_rowor.
+void join_features(const JoinShape& js, double rx, double ry, float* f, double* rho_out);
+double or_density(double rho, double n);
+
+// Tensor-core path or row-OR for a matrix-form cluster?  Forced by
+// pa_set_contract_path, else the faster by the context's measured rates: the
+// row-OR does (set bits of A) x (words per B row) word ORs, the tensor path
+// every multiply-add of its padded 128 x BN x 128 tiles (its rate includes
+// the expansion of both operands).  `ra` is A's estimated density (< 0:
+// unknown).
+bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
+  // no context (pa_solve_network_static): the row-OR, which needs no byte copies
+  if (!ctx || ctx->path == PA_PATH_ROWOR || tensor_map_encoder() == nullptr) return false;
+  const double M = (double)js.M, N = js.nbits, K = (double)js.K, nb = (double)js.nbatch;
+  if (nb * M >= 2147483647.0 || N >= 2147483647.0 || nb >= 2147483647.0) return false;
+  if (nb * (M + N) * (ceil(K / 128) * 128) > 4e9) return false;  // byte copies of the operands
+  if (ctx->path == PA_PATH_MMA) return true;
+  const double BN = N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  const double macs = nb * ceil(M / 128) * 128 * ceil(N / BN) * BN * ceil(K / 128) * 128;
+  if (macs < 134217728.0) return false;  // small clusters: the row-OR's launch is cheaper
+  const double dens = ra >= 0 ? ra : 0.05;
+  // the row-OR rate grows with density (per-bit overheads amortise): log-linear
+  // between the two measured points, constant outside them
+  const double f = std::min(1.0, std::max(0.0, log(std::max(dens, 1e-12) / 0.02) / log(8.0)));
+  const double rate_or = ctx->rate_or * pow(ctx->rate_or_dense / ctx->rate_or, f);
+  const double t_or = dens * M * K * nb * ceil(N / 64) / rate_or;
+  const double t_mma = macs / ctx->rate_mma;
+  return t_mma < t_or;
+}
+
+// rx, ry: estimated densities of X and Y (< 0: unknown); *rho_out receives the
+// estimated density of the result when both are known.
 BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
-            const std::vector<int64_t>& vres, const BitArr* target, int64_t target_ctas) {
+            const std::vector<int64_t>& vres, const BitArr* target, int64_t target_ctas,
+            double rx = -1.0, double ry = -1.0, double* rho_out = nullptr) {
   const JoinShape js = analyze_join(X, Y, keep, vres);
   bd.st.pixel_ops_dense += js.cost;
   bd.st.n_joins++;
+  double ra = -1.0;
+  if (rx >= 0 && ry >= 0) {
+    float f[PA_FEATURES];
+    join_features(js, rx, ry, f, rho_out);
+    ra = or_density(js.swap ? ry : rx, js.private_a);
+  }
 
   if (js.hadamard) {
     bool use_target = target && target->w && target->ndim == (int)keep.size();
@@ -555,6 +650,27 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
   if (target && target->w && same_layout(C, *target)) C.w = target->w;
   else C.w = bd.alloc_words(C.words());
 
+  if (use_mma(bd.ctx, js, ra)) {
+    MmaDesc md;
+    memset(&md, 0, sizeof md);
+    md.A = Am.w;
+    md.B = Bm.w;
+    md.C = C.w;
+    md.M = js.M;
+    md.N = (int64_t)js.nbits;
+    md.K = js.K;
+    md.a_row_words = Am.row_words();
+    md.nbatch = js.nbatch;
+    md.err = bd.d_err;
+    mma_plan(md);
+    md.Ab = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.M * md.Kp)));
+    md.Bb = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.N * md.Kp)));
+    bd.pend_mma.push_back(md);
+    bd.st.mma_macs += (double)js.nbatch * (double)js.M * js.nbits * (double)js.K;
+    bd.st.n_mma++;
+    bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
+    return C;
+  }
   RowOrDesc d;
   memset(&d, 0, sizeof d);
   d.A = Am.w;
@@ -772,7 +888,21 @@ struct Network {
   const int32_t* pairs;
   BitArr target;
   std::vector<int32_t> own_pairs;  // orders chosen by the learned planner
+  std::vector<double> dens_cache;  // estimated plot densities (both passes of a call share them)
+  std::vector<uint64_t> slot_keys;  // per slot: key of the relations and kept variables below it
 };
+
+std::vector<double> plot_densities(const Network& n, pa_ctx* ctx);
+uint64_t relation_key(const pa_relation& r, const pa_axis* axes);
+uint64_t mix64(uint64_t z);
+
+// Key of a join's result: its two operands' keys (in either order) and the
+// variables it keeps.
+uint64_t subtree_key(uint64_t ka, uint64_t kb, const std::vector<int>& keep) {
+  uint64_t h = mix64(std::min(ka, kb) ^ 0x5bd1e995ull) ^ (std::max(ka, kb) * 0x9E3779B97F4A7C15ull);
+  for (int v : keep) h = mix64(h ^ (uint64_t)(uint32_t)v);
+  return h;
+}
 
 // Plots of all networks in one launch pair, then their joins level by level:
 // the joins of one level of every network's cluster tree are independent and
@@ -789,6 +919,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
     std::vector<int64_t> vres;
     std::vector<BitArr> slots;
     std::vector<int> level;
+    std::vector<double> dens;  // estimated slot densities (empty: not needed)
   };
   std::vector<State> S(nets.size());
   int max_level = 0;
@@ -809,10 +940,27 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
     const int nj = (int)s.plan.joins.size();
     s.slots.resize(n.nrel + nj);
     s.level.assign(n.nrel + nj, 0);
+    bool large = false;
     for (int t = 0; t < nj; ++t) {
       const Join& jn = s.plan.joins[t];
       s.level[n.nrel + t] = 1 + std::max(s.level[jn.a], s.level[jn.b]);
       max_level = std::max(max_level, s.level[n.nrel + t]);
+      large = large || jn.cost >= 134217728.0;
+    }
+    // the automatic path choice weighs densities, estimated only where a
+    // cluster is large enough for the tensor-core path to be considered
+    if (large && bd.ctx && bd.ctx->path == PA_PATH_AUTO) {
+      if (n.dens_cache.empty()) n.dens_cache = plot_densities(n, bd.ctx);
+      s.dens = n.dens_cache;
+      s.dens.resize(n.nrel + nj, -1.0);
+    }
+    if (bd.ctx && (!s.dens.empty() || join_results)) {
+      n.slot_keys.assign(n.nrel + nj, 0);
+      for (int i = 0; i < n.nrel; ++i) n.slot_keys[i] = relation_key(n.rels[i], n.axes);
+      for (int t = 0; t < nj; ++t) {
+        const Join& jn = s.plan.joins[t];
+        n.slot_keys[n.nrel + t] = subtree_key(n.slot_keys[jn.a], n.slot_keys[jn.b], jn.keep);
+      }
     }
   }
   for (int lv = 1; lv <= max_level; ++lv) {
@@ -829,9 +977,17 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
         const Join& jn = s.plan.joins[t];
         const bool last = (t + 1 == nj);
         const size_t first_op = bd.ops.size();
+        const bool dn = !s.dens.empty();
         s.slots[nrel + t] = join(bd, s.slots[jn.a], s.slots[jn.b], jn.keep, s.vres,
                                  last ? &nets[k].target : nullptr,
-                                 one_join_per_launch ? 152 : target_ctas);
+                                 one_join_per_launch ? 152 : target_ctas,
+                                 dn ? s.dens[jn.a] : -1.0, dn ? s.dens[jn.b] : -1.0,
+                                 dn ? &s.dens[nrel + t] : nullptr);
+        if (dn) {
+          // a density measured by pa_join_log beats the independence estimate
+          auto it = bd.ctx->obs_dens.find(nets[k].slot_keys[nrel + t]);
+          if (it != bd.ctx->obs_dens.end()) s.dens[nrel + t] = it->second;
+        }
         if (one_join_per_launch) {
           flush_rowor(bd);
           for (size_t q = first_op; q < bd.ops.size(); ++q) bd.ops[q].join = t;
@@ -894,6 +1050,16 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
         break;
       case OP_DOT:
         launch_dot(op.a, op.b, op.p, op.count, op.m, op.nw, s);
+        break;
+      case OP_UNPACK:
+        launch_unpack(reinterpret_cast<const MmaDesc*>(blob + op.off0), op.n, op.m, op.nw, s);
+        break;
+      case OP_MMA:
+        check_cuda(ctx,
+                   launch_mma(reinterpret_cast<const MmaDesc*>(blob + op.off0),
+                              reinterpret_cast<const CUtensorMap*>(blob + op.off1),
+                              reinterpret_cast<const int64_t*>(blob + op.off2), op.n, op.count, s),
+                   "mma_bool_kernel");
         break;
       case OP_ROWOR:
         check_cuda(ctx,
@@ -1175,10 +1341,53 @@ Plan plan_of(const Network& n, int order, const int32_t* pairs, uint64_t policy)
   return plan_joins_policy(n.nvars, vresd, rv, n.exposed, order, pairs, policy);
 }
 
-std::vector<double> plot_densities(const Network& n) {
+// Key of a relation's density estimate: its arity, degree, kind, eps,
+// coefficients and the boxes and resolutions of its variables (SplitMix64
+// finaliser over the bytes, 8 at a time).
+uint64_t relation_key(const pa_relation& r, const pa_axis* axes) {
+  uint64_t h = 0x160900061ull;
+  auto add = [&](uint64_t v) { h = mix64(h ^ v); };
+  auto addd = [&](double x) {
+    uint64_t v;
+    memcpy(&v, &x, 8);
+    add(v);
+  };
+  add((uint64_t)r.arity << 32 | (uint32_t)r.degree);
+  add((uint64_t)r.kind);
+  addd(r.eps);
+  for (int p = 0; p < r.arity; ++p) {
+    const pa_axis& a = axes[r.vars[p]];
+    addd(a.lo);
+    addd(a.hi);
+    add((uint64_t)a.res << 8 | (uint64_t)p);
+  }
+  const int64_t nc = coeff_count(r.arity, r.degree);
+  for (int64_t i = 0; i < nc; ++i) addd(r.coeffs[i]);
+  return h;
+}
+
+// Estimated plot densities of a network's relations; with a context, kept in
+// its cache so that solving the same relations again skips the sampling.
+std::vector<double> plot_densities(const Network& n, pa_ctx* ctx) {
   std::vector<double> d;
-  for (int i = 0; i < n.nrel; ++i)
-    d.push_back(estimate_density(n.rels[i], n.axes, relation_eps(n.rels[i], n.axes)));
+  for (int i = 0; i < n.nrel; ++i) {
+    const pa_relation& r = n.rels[i];
+    uint64_t key = 0;
+    if (ctx) {
+      key = relation_key(r, n.axes);
+      auto it = ctx->dens_cache.find(key);
+      if (it != ctx->dens_cache.end()) {
+        d.push_back(it->second);
+        continue;
+      }
+    }
+    const double v = estimate_density(r, n.axes, relation_eps(r, n.axes));
+    if (ctx) {
+      if (ctx->dens_cache.size() >= (1u << 16)) ctx->dens_cache.clear();
+      ctx->dens_cache[key] = v;
+    }
+    d.push_back(v);
+  }
   return d;
 }
 
@@ -1203,7 +1412,7 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
   for (size_t k = 0; k < nets.size(); ++k) {
     const Network& n = nets[k];
     first[k] = cands.size();
-    const std::vector<double> dens = plot_densities(n);
+    const std::vector<double> dens = plot_densities(n, ctx);
     std::vector<std::vector<int32_t>> seen;
     for (int c = 0; c < ncand; ++c) {
       Plan p = (c == 0) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 0)
@@ -1359,6 +1568,170 @@ void pa_destroy(pa_ctx* ctx) {
 }
 
 const char* pa_last_error(const pa_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pa_status pa_set_contract_path(pa_ctx* ctx, int32_t path) {
+  if (!ctx) return PA_ERR_INVALID_ARG;
+  if (path != PA_PATH_AUTO && path != PA_PATH_ROWOR && path != PA_PATH_MMA)
+    return set_err(ctx, PA_ERR_INVALID_ARG, "contract path must be PA_PATH_AUTO, _ROWOR or _MMA");
+  ctx->path = path;
+  return PA_OK;
+}
+
+pa_status pa_get_rates(const pa_ctx* ctx, pa_rates* out) {
+  if (!ctx || !out) return PA_ERR_INVALID_ARG;
+  out->rowor_words_per_us = ctx->rate_or;
+  out->rowor_words_per_us_dense = ctx->rate_or_dense;
+  out->mma_macs_per_us = ctx->rate_mma;
+  return PA_OK;
+}
+
+pa_status pa_set_rates(pa_ctx* ctx, const pa_rates* r) {
+  if (!ctx || !r) return PA_ERR_INVALID_ARG;
+  for (double v : {r->rowor_words_per_us, r->rowor_words_per_us_dense, r->mma_macs_per_us})
+    if (!(v > 0) || !isfinite(v))
+      return set_err(ctx, PA_ERR_INVALID_ARG, "rates must be finite and positive");
+  ctx->rate_or = r->rowor_words_per_us;
+  ctx->rate_or_dense = r->rowor_words_per_us_dense;
+  ctx->rate_mma = r->mma_macs_per_us;
+  return PA_OK;
+}
+
+pa_status pa_autotune(pa_ctx* ctx, pa_rates* out, void* stream) {
+  if (!ctx) return PA_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PA_ERR_CUDA, "cudaSetDevice failed");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr int64_t R = 2048, W = R / 64;
+  uint64_t *A = nullptr, *B = nullptr, *C = nullptr;
+  uint8_t *Ab = nullptr, *Bb = nullptr;
+  char* tab = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  pa_status st = PA_OK;
+  auto fail = [&](const char* what) {
+    cudaGetLastError();
+    st = set_err(ctx, PA_ERR_CUDA, std::string("autotune: ") + what);
+  };
+  // time `reps` runs of f after one warm-up
+  auto time_us = [&](auto&& f, int reps) -> double {
+    f();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) f();
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms * 1000.0 / reps;
+  };
+  do {
+    if (cudaMalloc(&A, R * W * 8) != cudaSuccess || cudaMalloc(&B, R * W * 8) != cudaSuccess ||
+        cudaMalloc(&C, R * W * 8) != cudaSuccess || cudaMalloc(&tab, 4096) != cudaSuccess ||
+        cudaMalloc(&Ab, R * R) != cudaSuccess || cudaMalloc(&Bb, R * R) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      fail("device allocation failed");
+      break;
+    }
+    launch_random_bits(B, R * W, W, R, 0.02, 0x260900061ull, s);
+    // row-OR: words OR-ed counted by the kernel
+    RowOrDesc rd;
+    memset(&rd, 0, sizeof rd);
+    rd.A = A;
+    rd.B = B;
+    rd.C = C;
+    rd.nbatch = 1;
+    rd.M = R;
+    rd.K = R;
+    rd.Nw = W;
+    rd.a_row_words = W;
+    rd.err = ctx->d_err;
+    rd.stat = ctx->d_stat;
+    rowor_plan(rd, 152);
+    CUtensorMap rmap;
+    if (rowor_encode_map(rd, &rmap) != cudaSuccess) {
+      fail("tensor map (row-OR)");
+      break;
+    }
+    const int64_t rcta[2] = {0, rowor_ctas(rd)};
+    MmaDesc md;
+    memset(&md, 0, sizeof md);
+    md.A = A;
+    md.B = B;
+    md.C = C;
+    md.M = R;
+    md.N = R;
+    md.K = R;
+    md.a_row_words = W;
+    md.nbatch = 1;
+    md.err = ctx->d_err;
+    mma_plan(md);
+    md.Ab = Ab;
+    md.Bb = Bb;
+    CUtensorMap mmaps[2];
+    if (mma_encode_maps(md, mmaps) != cudaSuccess) {
+      fail("tensor maps (tensor-core path)");
+      break;
+    }
+    const int64_t mcta[2] = {0, mma_ctas(md)};
+    // pageable sources: each copy returns once the driver has taken the bytes
+    cudaMemcpyAsync(tab, &rd, sizeof rd, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tab + 1024, &rmap, sizeof rmap, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tab + 2048, rcta, sizeof rcta, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tab + 3072, &md, sizeof md, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tab + 2048 + 64, mcta, sizeof mcta, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tab + 1024 + 128, mmaps, sizeof mmaps, cudaMemcpyHostToDevice, s);
+    const size_t rsmem = rowor_smem_bytes(rd);
+    const int reps = 5;
+    // row-OR at two densities of A (words OR-ed counted by the kernel)
+    double rate_or[2] = {0, 0};
+    const double dens[2] = {0.02, 0.16};
+    for (int i = 0; i < 2; ++i) {
+      launch_random_bits(A, R * W, W, R, dens[i], 0x160900061ull + i, s);
+      unsigned long long zero = 0, words = 0;
+      cudaMemcpyAsync(ctx->d_stat, &zero, sizeof zero, cudaMemcpyHostToDevice, s);
+      const double t_or = time_us(
+          [&] {
+            launch_rowor(reinterpret_cast<const RowOrDesc*>(tab),
+                         reinterpret_cast<const CUtensorMap*>(tab + 1024),
+                         reinterpret_cast<const int64_t*>(tab + 2048), 1, rcta[1], rsmem, rd.Nt, s);
+          },
+          reps);
+      cudaMemcpy(&words, ctx->d_stat, sizeof words, cudaMemcpyDeviceToHost);
+      cudaMemset(ctx->d_stat, 0, sizeof words);
+      if (t_or > 0 && words > 0) rate_or[i] = (double)words / (reps + 1) / t_or;
+    }
+    // the tensor path's rate includes expanding both operands
+    const double t_mma = time_us(
+        [&] {
+          launch_unpack(reinterpret_cast<const MmaDesc*>(tab + 3072), 1, unpack_blocks_a(md),
+                        unpack_blocks_b(md), s);
+          launch_mma(reinterpret_cast<const MmaDesc*>(tab + 3072),
+                     reinterpret_cast<const CUtensorMap*>(tab + 1024 + 128),
+                     reinterpret_cast<const int64_t*>(tab + 2048 + 64), 1, mcta[1], s);
+        },
+        reps);
+    if (cudaGetLastError() != cudaSuccess || rate_or[0] <= 0 || rate_or[1] <= 0 || t_mma <= 0) {
+      fail("timing runs failed");
+      break;
+    }
+    int herr = 0;
+    cudaMemcpy(&herr, ctx->d_err, sizeof herr, cudaMemcpyDeviceToHost);
+    if (herr) {
+      st = set_err(ctx, PA_ERR_TIMEOUT, "autotune: a bounded device wait ran out");
+      cudaMemset(ctx->d_err, 0, sizeof herr);
+      break;
+    }
+    ctx->rate_or = rate_or[0];
+    ctx->rate_or_dense = rate_or[1];
+    ctx->rate_mma = (double)R * R * R / t_mma;
+  } while (false);
+  if (st == PA_OK && out) pa_get_rates(ctx, out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (void* p : {(void*)A, (void*)B, (void*)C, (void*)Ab, (void*)Bb, (void*)tab})
+    if (p) cudaFree(p);
+  return st;
+}
 
 pa_status pa_profile_enable(pa_ctx* ctx, int32_t on) {
   if (!ctx) return PA_ERR_INVALID_ARG;
@@ -1837,12 +2210,20 @@ pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts,
       if (bd.ops[q].join >= 0 && bd.ops[q].join < nj) us[bd.ops[q].join] += 1000.0 * ms;
     }
     const Plan plan = plan_of(nets[0], nets[0].order, nets[0].pairs, 0);
-    const SimResult sim = simulate_plan(nets[0], plan, plot_densities(nets[0]));
+    const SimResult sim = simulate_plan(nets[0], plan, plot_densities(nets[0], ctx));
     *njoins = nj;
     for (int t = 0; t < nj && t < max_joins; ++t) {
       for (int k = 0; k < kFeat; ++k) features[t * kFeat + k] = sim.feats[t * kFeat + k];
       micros[t] = (float)us[t];
       densities[t] = (float)((double)cnt[t] / (double)std::max<int64_t>(1, results[t].bits()));
+    }
+    // remember the measured densities for later path choices on these relations
+    const Network& n0 = nets[0];
+    if ((int)n0.slot_keys.size() == n0.nrel + nj) {
+      if (ctx->obs_dens.size() >= (1u << 16)) ctx->obs_dens.clear();
+      for (int t = 0; t < nj; ++t)
+        ctx->obs_dens[n0.slot_keys[n0.nrel + t]] =
+            (double)cnt[t] / (double)std::max<int64_t>(1, results[t].bits());
     }
   } catch (const Fail& f) {
     st = f.st;

@@ -516,11 +516,6 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
 
 namespace {
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   static bool tried = false;
@@ -541,6 +536,8 @@ EncodeTiledFn encode_fn() {
 constexpr size_t kTileBudget = 156 * 1024;  // shared bytes for one B tile (the lists take 68 KB more)
 
 }  // namespace
+
+EncodeTiledFn tensor_map_encoder() { return encode_fn(); }
 
 void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
   // widest power-of-two tile (<= 32 words, <= the row) whose K range fits the budget

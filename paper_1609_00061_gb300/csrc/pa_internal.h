@@ -165,6 +165,46 @@ cudaError_t rowor_encode_map(const RowOrDesc& d, CUtensorMap* map);
 cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
                          const int64_t* d_cta0, int nprob, int64_t grid, size_t smem, int Nt,
                          cudaStream_t s);
+// cuTensorMapEncodeTiled from the driver (null when unavailable)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
+
+// Tensor-core contraction (mma.cu): the same problem as RowOrDesc, from the
+// same bit-packed layouts, as a 0/1 E4M3 matrix product thresholded at > 0.
+// The operands are first expanded into the byte arrays Ab and Bb.
+struct MmaDesc {
+  const uint64_t* A;          // [nbatch][M][a_row_words], K bits per row
+  const uint64_t* B;          // [nbatch][K][Nw], N bits per row
+  uint64_t* C;                // [nbatch][M][Nw]
+  uint8_t* Ab;                // [nbatch][M][Kp] E4M3 bytes
+  uint8_t* Bb;                // [nbatch][N][Kp] E4M3 bytes
+  int64_t M, N, K, Kp, Nw, a_row_words, nbatch;
+  int64_t m_tiles, n_tiles;
+  int32_t BN;                 // columns per tile: 64, 128 or 256
+  int* err;                   // device error word: set when a bounded wait runs out
+};
+void mma_plan(MmaDesc& d);    // BN, Nw, Kp and the tile counts from M, N, K, nbatch
+int64_t mma_ctas(const MmaDesc& d);
+size_t mma_smem_bytes();
+// TMA descriptors of Ab and Bb (needs d.Ab, d.Bb set)
+cudaError_t mma_encode_maps(const MmaDesc& d, CUtensorMap* maps2);
+// Expand A and B of every problem of a table into Ab and Bb (two launches;
+// blocks per problem from unpack_blocks_a / _b, the largest over the table).
+int64_t unpack_blocks_a(const MmaDesc& d);
+int64_t unpack_blocks_b(const MmaDesc& d);
+void launch_unpack(const MmaDesc* d_descs, int nprob, int64_t blocks_a, int64_t blocks_b,
+                   cudaStream_t s);
+// Independent problems in one launch: descriptors, two tensor maps per problem
+// and CTA offsets (nprob + 1 entries) on the device.
+cudaError_t launch_mma(const MmaDesc* d_descs, const CUtensorMap* d_maps, const int64_t* d_cta0,
+                       int nprob, int64_t grid, cudaStream_t s);
+// Random bit rows of the given density (autotuning inputs); padding stays zero.
+void launch_random_bits(uint64_t* w, int64_t nwords, int64_t row_words, int64_t valid,
+                        double density, uint64_t seed, cudaStream_t s);
+
 // cudaSuccess when this build holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
