@@ -75,7 +75,7 @@ pa_status set_err(pa_ctx* ctx, pa_status st, const std::string& msg) {
 bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
 // ------------------------------------------------------------ program
-enum OpKind { OP_PREP, OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
+enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
               OP_MMA };
 
 struct Op {
@@ -95,7 +95,6 @@ struct Op {
 
 const char* op_name(const Op& op) {
   switch (op.kind) {
-    case OP_PREP: return "plot_prep_kernel";
     case OP_PLOT: return "plot_kernel";
     case OP_MEMSET: return "memset";
     case OP_RESHAPE:
@@ -767,7 +766,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<size_t> coeff_off(nrel);
-  int64_t tiles = 0, prep_items = 0;
+  int64_t tiles = 0;
   int max_rows = 1, max_deg = 0, common_deg = reqs[0].rel->degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = *reqs[i].rel;
@@ -807,18 +806,10 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
     J.nrows = a.nrows();
     J.row_words = a.row_words();
     const int64_t res_last = a.res[a.ndim - 1];
-    const int D1 = r.degree + 1;
-    if (J.hoisted) {
-      J.g64 = static_cast<double*>(bd.alloc((size_t)J.nrows * D1 * 8));
-      J.g32 = static_cast<float*>(bd.alloc((size_t)J.nrows * D1 * 4));
-      J.thr = static_cast<float*>(bd.alloc((size_t)J.nrows * 2 * 4));
-      J.y32 = static_cast<float*>(bd.alloc((size_t)res_last * 4));
-      J.prep0 = prep_items;
-      prep_items += J.nrows + res_last;
-    }
     {
       const pa_axis& ax = axes[r.vars[r.arity - 1]];
       J.ymax = (float)(fmax(fabs(ax.lo), fabs(ax.hi)) * (1.0 + 0x1p-20));
+      J.hword = (float)(32.0 * ((ax.hi - ax.lo) / (double)ax.res) * 1.01);
       // coefficients with e_last = j form block j of the nest order; its size is
       // the number of monomials of arity-1 variables of degree <= D - j
       int32_t off = 0;
@@ -827,7 +818,9 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
         off += (int32_t)coeff_count(r.arity - 1, r.degree - j);
       }
     }
-    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, 512 / J.row_words));
+    // about 2048 words per block: the block's set-up (centre table, row
+    // polynomials) is spread over enough words
+    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(256, 2048 / J.row_words));
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
@@ -847,22 +840,10 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
     bd.st.pixels_plotted += (double)a.bits();
     bd.st.n_plots++;
   }
-  // prep items are assigned to jobs by binary search on prep0: give the jobs
-  // without preparation work the offset of the next one so the search skips them
-  for (int i = nrel - 1; i >= 0; --i)
-    if (!jobs[i].hoisted) jobs[i].prep0 = (i + 1 < nrel) ? jobs[i + 1].prep0 : prep_items;
   if (tiles > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "plot grid too large");
   for (int i = 0; i < nrel; ++i)
     jobs[i].coeffs = reinterpret_cast<const double*>(bd.dev(coeff_off[i]));
   const size_t jobs_off = bd.put(jobs.data(), jobs.size(), 64);
-  if (prep_items > 0) {
-    Op op;
-    op.kind = OP_PREP;
-    op.off0 = jobs_off;
-    op.n = nrel;
-    op.count = prep_items;
-    bd.ops.push_back(op);
-  }
   Op op;
   op.kind = OP_PLOT;
   op.off0 = jobs_off;
@@ -1029,9 +1010,6 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
       check_cuda(ctx, cudaEventRecord(rec.a, s), "cudaEventRecord");
     }
     switch (op.kind) {
-      case OP_PREP:
-        launch_plot_prep(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, s);
-        break;
       case OP_PLOT:
         launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
                     op.i1, op.i2, op.i3, s);

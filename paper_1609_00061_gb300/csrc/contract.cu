@@ -562,7 +562,9 @@ void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
   d.atomic = d.k_chunks > 1 ? 1 : 0;
   const int64_t base = d.nbatch * d.n_tiles * d.k_chunks;
   const int64_t target = std::max<int64_t>(1, target_ctas);
-  int64_t splits = (target + base - 1) / base;
+  // round down: a launch of more CTAs than SMs (one CTA fits an SM) would run
+  // a short second wave and nearly double its time
+  int64_t splits = target / base;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, (d.M + 15) / 16));
   d.rows_per_split = (d.M + splits - 1) / splits;
   d.row_splits = (d.M + d.rows_per_split - 1) / d.rows_per_split;

@@ -29,15 +29,9 @@ struct PlotJob {
   uint64_t* out;                    // device, pa_array layout
   double lo[kMaxDim];               // per port: range start of its variable
   double delta[kMaxDim];            // per port: pixel width of its variable
-  // per-row data written by the preparation kernel (hoisted jobs only)
-  double* g64;                      // [nrows][D+1] row polynomial in the last port
-  float* g32;                       // [nrows][D+1] its FP32 copy
-  float* thr;                       // [nrows][2] FP32 thresholds eps -+ B_row
-  float* y32;                       // [res_last] FP32 centres of the last port
   int64_t nrows;                    // rows = product of all but the last array axis
   int64_t row_words;                // ceil(res_last / 64)
   int64_t tile0;                    // first block of this job in the plot launch
-  int64_t prep0;                    // first item of this job in the preparation launch
   int32_t rows_per_tile;
   int32_t arity, degree, kind, strict;
   int32_t hoisted;                  // 1: the last port is the last array axis, used once
@@ -49,14 +43,14 @@ struct PlotJob {
   float kfac;                       // FP32 filter: error bound factor on sum |g_j| Y^j
   float abs_margin;                 // FP32 filter: margin for eps rounding / underflow
   float ymax;                       // >= |y| for every FP32 centre of the last port
+  float hword;                      // >= distance from a word's pixel 32 to any of its 64 centres
   int32_t block_off[kMaxDeg + 1];   // nest-order offset of the coefficients with e_last = j
 };
 
-// prep: per-row polynomials and thresholds, FP32 centre tables (one item per
-// row and one per last-axis pixel of every hoisted job); plot: the pixels.
-void launch_plot_prep(const PlotJob* d_jobs, int njobs, int64_t total_items, cudaStream_t s);
-// common_degree: the degree shared by every job (selects a specialised kernel),
-// or -1 when they differ
+// One launch plots every job: blocks of rows_per_tile rows, each computing its
+// rows' polynomials and thresholds in shared memory first.  common_degree: the
+// degree shared by every job (selects a specialised kernel), or -1 when they
+// differ.
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, cudaStream_t s);
 

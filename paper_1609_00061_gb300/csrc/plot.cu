@@ -11,8 +11,9 @@
 // Row hoisting: with every port but the last fixed, f is a polynomial
 // f = sum_j g_j y^j in the last port y.  The g_j are exactly the inner nested
 // sums of the pa.h evaluation order, so computing them once per row in FP64
-// and finishing each pixel with sum_j g_j y^j performs the very same IEEE
-// operations as evaluating the pixel from scratch.
+// (at the start of the block that plots the row) and finishing each pixel with
+// sum_j g_j y^j performs the very same IEEE operations as evaluating the pixel
+// from scratch.
 //
 // Error bound for the FP32 pass (u = 2^-24, D the degree, g_j rounded to FP32,
 // y32 = fl32(y64), a = sum_j |g_j| |y|^j):
@@ -22,6 +23,21 @@
 // and a <= a_row = sum_j |g_j| Y^j with Y >= |y| on the whole axis.  The kernel
 // uses B_row = (4D + 8) u 1.01 a_row + 2^-21 eps + 1e-30, which also covers the
 // rounding of a_row, of eps to FP32 and of the thresholds themselves.
+//
+// Whole-word pruning (the paper's suggestion of skipping regions whose error
+// provably exceeds eps, here per 64-pixel word).  With F the exact row
+// polynomial, y_c the word's pixel 32 and h >= the distance from y_c to any
+// centre of the word, Taylor's theorem gives for every pixel y of the word
+//   |F(y) - F(y_c)| <= h |F'(y_c)| + h^2 / 2 max |F''|,
+// max |F''| <= S2 = sum_j j (j-1) |g_j| Yw^(j-2) with Yw = |y_c| + h, and the
+// FP32 derivative d_c (Horner) satisfies |d_c - F'(y_c)| <= (2D + 4) u S1,
+// S1 = sum_j j |g_j| |y_c|^(j-1).  With T = 1.01 (h (|d_c| + (2D+4) u S1) +
+// h^2 S2 / 2) and the pixel bound B_row used three times (f32 vs f64 at y_c,
+// f64 vs F at y_c and at y):
+//   |f64(y) - f32(y_c)| <= 3 B_row + T,
+// so f32(y_c) beyond eps + B_row + 4 B_row + T proves the whole word off (|f|
+// for PA_EQ), and for PA_LE / PA_LT f32(y_c) below eps - B_row - 4 B_row - T
+// proves it on; only the remaining words are evaluated pixel by pixel.
 #include <float.h>
 
 #include "pa_internal.h"
@@ -110,89 +126,41 @@ __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i)
   return decide64(nest_dev(J->arity - 1, J->degree, cp, x), J->kind, J->eps, J->strict);
 }
 
-// ------------------------------------------------------------- preparation
-// Items of job j: rows 0..nrows-1 (row polynomial and thresholds), then the
-// res_last pixels of the last port (FP32 centre table).
-__global__ void __launch_bounds__(256)
-plot_prep_kernel(const PlotJob* __restrict__ jobs, int njobs, int64_t total) {
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-       it += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].prep0 <= it) lo = mid; else hi = mid - 1;
-    }
-    const PlotJob* J = jobs + lo;
-    const int64_t k = it - J->prep0;
-    const int arity = J->arity, D = J->degree, D1 = D + 1;
-    if (k < J->nrows) {
-      const int64_t row = k;
-      int64_t rest = row;
-      int64_t idx[kMaxDim];
-      for (int a = J->ndim - 2; a >= 0; --a) {
-        idx[a] = rest % J->res[a];
-        rest /= J->res[a];
-      }
-      double x[kMaxDim];
-      for (int p = 0; p < arity - 1; ++p)
-        x[p] = centre(J->lo[p], J->delta[p], idx[J->port_axis[p]]);
-      const double* cp = J->coeffs;
-      const float Y = J->ymax;
-      float a = 0.0f, pw = 1.0f;
-      for (int j = 0; j <= D; ++j) {
-        const double g = nest_rows(arity - 2, D - j, cp, x);  // cp walks block j
-        const float g1 = __double2float_rn(g);
-        J->g64[row * D1 + j] = g;
-        J->g32[row * D1 + j] = g1;
-        a = __fmaf_rn(fabsf(g1), pw, a);
-        pw = __fmul_rn(pw, Y);
-      }
-      const float B = __fmaf_rn(a, J->kfac, J->abs_margin);
-      float tlo = __fsub_rn(J->eps32, B), thi = __fadd_rn(J->eps32, B);
-      if (!(a <= FLT_MAX) || !(B <= FLT_MAX)) {
-        tlo = -INFINITY;  // nothing is certain: every pixel of the row takes the FP64 path
-        thi = INFINITY;
-      }
-      J->thr[2 * row] = tlo;
-      J->thr[2 * row + 1] = thi;
-    } else {
-      const int64_t i = k - J->nrows;
-      J->y32[i] = __double2float_rn(centre(J->lo[arity - 1], J->delta[arity - 1], i));
-    }
-  }
-}
-
-void launch_plot_prep(const PlotJob* d_jobs, int njobs, int64_t total_items, cudaStream_t s) {
-  if (total_items <= 0) return;
-  int64_t blocks = (total_items + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  plot_prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total_items);
-}
-
 // --------------------------------------------------------------- plot kernel
-// One block plots a tile of rows: the FP32 centres of the last axis are staged
-// in shared memory (padded so that consecutive words hit distinct banks), then
-// each thread evaluates whole output words: the 64 pixels of a word in FP32
-// (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below eps - B_row is on,
-// above eps + B_row is off, anything else is decided by the exact FP64
-// evaluation.  Bits are set directly in the thread's word, so no warp vote is
-// needed and a row's words are stored coalesced.
+// One block plots a tile of rows.  Set-up: the FP32 centres of the last axis
+// are staged in shared memory (padded so that consecutive words hit distinct
+// banks) and each row's polynomial and thresholds are computed there.  Then
+// each thread takes whole output words: the whole-word test first, else the
+// 64 pixels in FP32 (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below
+// eps - B_row is on, above eps + B_row is off, anything else is decided by the
+// exact FP64 evaluation.  Bits are set directly in the thread's word, so no
+// warp vote is needed and a row's words are stored coalesced.
 constexpr int kPlotThreads = 256;
 constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
 
 __device__ __forceinline__ int ypad(int i) { return i + (i >> 6); }
 
+// Byte offset of the thresholds in a plot block's shared memory (16-aligned).
+__host__ __device__ __forceinline__ size_t plot_thr_offset(int rmax, int gstride) {
+  return ((size_t)rmax * gstride * 12 + 15) / 16 * 16;
+}
+
 // The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
 // certainly on, bit b of *pending when only the FP64 evaluation can decide.
+// The FP32 centre of last-axis pixel i (the table entry when staged).
+__device__ __forceinline__ float ycentre32(double ylo, double ydelta, int i) {
+  return __double2float_rn(centre(ylo, ydelta, i));
+}
+
 template <int DS, bool EQ, bool YS, bool FULL>
 __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
-                                          const float* ytab_w, const float* __restrict__ y32_w,
+                                          const float* ytab_w, double ylo, double ydelta, int i0,
                                           int nb, uint64_t* on, uint64_t* pending) {
   uint32_t on_lo = 0, on_hi = 0, pe_lo = 0, pe_hi = 0;
 #pragma unroll
   for (int bb = 0; bb < 64; ++bb) {
     if (FULL || bb < nb) {
-      const float y = YS ? ytab_w[bb] : __ldg(y32_w + bb);
+      const float y = YS ? ytab_w[bb] : ycentre32(ylo, ydelta, i0 + bb);
       float s = g[0], pw = y;
       if (DS >= 0) {
 #pragma unroll
@@ -224,16 +192,22 @@ __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float
 
 template <int DS, bool EQ, bool YS>
 __device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, float hi,
-                                              const float* ytab_w, const float* y32_w, int nb,
-                                              uint64_t* on, uint64_t* pending) {
-  if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, y32_w, nb, on, pending);
-  else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, y32_w, nb, on, pending);
+                                              const float* ytab_w, double ylo, double ydelta,
+                                              int i0, int nb, uint64_t* on, uint64_t* pending) {
+  if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, on, pending);
+  else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, on, pending);
 }
 
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
-plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap) {
-  extern __shared__ __align__(16) float ytab[];
+plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstride, int rmax) {
+  extern __shared__ __align__(16) unsigned char plot_smem[];
+  // [rmax][gstride] FP64 row polynomials, [rmax][gstride] FP32 copies,
+  // [rmax] thresholds, then the padded FP32 centre table
+  double* g64s = reinterpret_cast<double*>(plot_smem);
+  float* g32s = reinterpret_cast<float*>(g64s + (size_t)rmax * gstride);
+  float4* thrs = reinterpret_cast<float4*>(plot_smem + plot_thr_offset(rmax, gstride));
+  float* ytab = reinterpret_cast<float*>(thrs + rmax);
   __shared__ int s_job;
   if (threadIdx.x == 0) {
     int lo = 0, hi = njobs - 1;
@@ -246,7 +220,6 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap) {
   __syncthreads();
   const PlotJob* J = jobs + s_job;
   const int D = DS >= 0 ? DS : J->degree;
-  const int D1 = D + 1;
   const int row_words = (int)J->row_words;
   const int res_last = J->res[J->ndim - 1];
   const int R = J->rows_per_tile;
@@ -254,14 +227,49 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap) {
   const int nr = (int)min((int64_t)R, J->nrows - row0);
   const bool hoisted = J->hoisted != 0;
   const bool ysmem = hoisted && res_last <= ytab_cap;
-  const float* __restrict__ y32g = J->y32;
-  if (ysmem) {
-    for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = y32g[i];
+  const int arity = J->arity;
+  const double ylo = J->lo[arity - 1], ydelta = J->delta[arity - 1];
+  if (hoisted) {
+    // set-up: the centre table, and per row (one thread each) the row
+    // polynomial g_0..g_D in FP64 (the inner nested sums of the pa.h order),
+    // its FP32 copy and the row's thresholds eps -+ B_row
+    if (ysmem)
+      for (int i = threadIdx.x; i < res_last; i += blockDim.x)
+        ytab[ypad(i)] = ycentre32(ylo, ydelta, i);
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      int64_t rest = row0 + r;
+      int64_t idx[kMaxDim];
+      for (int a = J->ndim - 2; a >= 0; --a) {
+        idx[a] = rest % J->res[a];
+        rest /= J->res[a];
+      }
+      double x[kMaxDim];
+      for (int p = 0; p < arity - 1; ++p)
+        x[p] = centre(J->lo[p], J->delta[p], idx[J->port_axis[p]]);
+      const double* cp = J->coeffs;
+      const float Y = J->ymax;
+      float a = 0.0f, pw = 1.0f;
+      for (int j = 0; j <= D; ++j) {
+        const double g = nest_rows(arity - 2, D - j, cp, x);  // cp walks block j
+        const float g1 = __double2float_rn(g);
+        g64s[r * gstride + j] = g;
+        g32s[r * gstride + j] = g1;
+        a = __fmaf_rn(fabsf(g1), pw, a);
+        pw = __fmul_rn(pw, Y);
+      }
+      float B = __fmaf_rn(a, J->kfac, J->abs_margin);
+      float tlo = __fsub_rn(J->eps32, B), thi = __fadd_rn(J->eps32, B);
+      if (!(a <= FLT_MAX) || !(B <= FLT_MAX)) {
+        tlo = -INFINITY;  // nothing is certain: every pixel of the row takes the FP64 path
+        thi = INFINITY;
+        B = INFINITY;
+      }
+      thrs[r] = make_float4(tlo, thi, B, 0.0f);
+    }
     __syncthreads();
   }
   const int kind = J->kind, strict = J->strict;
   const double eps = J->eps;
-  const double ylo = J->lo[J->arity - 1], ydelta = J->delta[J->arity - 1];
   uint64_t* __restrict__ out = J->out;
   constexpr int kG = DS >= 0 ? DS + 1 : kMaxDeg + 1;
   const int nwords = nr * row_words;
@@ -273,24 +281,52 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap) {
     uint64_t word = 0;
     if (hoisted) {
       float g[kG];
-      const float* __restrict__ gr = J->g32 + row * D1;
+      const float* gr = g32s + r * gstride;
 #pragma unroll
-      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? __ldg(gr + j) : 0.0f;
-      const float lo = __ldg(J->thr + 2 * row), hi = __ldg(J->thr + 2 * row + 1);
+      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? gr[j] : 0.0f;
+      const float4 th = thrs[r];
+      const float lo = th.x, hi = th.y;
       uint64_t pending = 0;
       const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
-      const float* y32_w = y32g + i0;
+      if (nb == 64) {
+        // whole-word test at the middle pixel (see the header)
+        const float yc = ysmem ? ytab_w[32] : ycentre32(ylo, ydelta, i0 + 32);
+        const float h = J->hword, ya = fabsf(yc), yw = ya + h;
+        // Horner for F and F' at y_c; S1 at |y_c| and S2 at |y_c| + h
+        float fc = g[D], dc = 0.0f, s1 = 0.0f, s2 = 0.0f;
+        for (int j = D - 1; j >= 0; --j) {
+          dc = __fmaf_rn(dc, yc, fc);
+          fc = __fmaf_rn(fc, yc, g[j]);
+        }
+        for (int j = D; j >= 1; --j) s1 = __fmaf_rn(s1, ya, (float)j * fabsf(g[j]));
+        for (int j = D; j >= 2; --j) s2 = __fmaf_rn(s2, yw, (float)(j * (j - 1)) * fabsf(g[j]));
+        const float e1 = (float)(2 * D + 4) * 5.9604645e-8f * s1;  // (2D + 4) 2^-24 S1
+        const float taylor = __fmaf_rn(h, fabsf(dc) + e1, 0.5f * h * h * s2) * 1.01f;
+        const float margin = __fmaf_rn(4.0f, th.z, taylor);
+        if (kind == PA_EQ) {
+          if (fabsf(fc) > hi + margin) {
+            out[row * row_words + w] = 0ull;
+            continue;
+          }
+        } else if (fc > hi + margin) {
+          out[row * row_words + w] = 0ull;
+          continue;
+        } else if (fc < lo - margin) {
+          out[row * row_words + w] = ~0ull;
+          continue;
+        }
+      }
       if (kind == PA_EQ) {
-        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
-        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
+        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
       } else {
-        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
-        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, y32_w, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
+        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
       }
       while (pending) {
         const int bb = __ffsll((long long)pending) - 1;
         pending &= pending - 1;
-        if (exact64(centre(ylo, ydelta, i0 + bb), J->g64 + row * D1, D, kind, eps, strict))
+        if (exact64(centre(ylo, ydelta, i0 + bb), g64s + r * gstride, D, kind, eps, strict))
           word |= (1ull << bb);
       }
     } else {
@@ -308,13 +344,18 @@ cudaError_t probe_kernel_image() {
 
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, cudaStream_t s) {
-  (void)max_rows_per_tile;
-  (void)max_degree;
   if (total_tiles <= 0) return;
   const int ycap = max_res_last <= kYTabCap ? max_res_last : 0;
-  const size_t smem = (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
+  const int gstride = max_degree + 1, rmax = max_rows_per_tile;
+  const size_t smem = plot_thr_offset(rmax, gstride) + (size_t)rmax * 16 +
+                      (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
   const unsigned grid = (unsigned)total_tiles;
-#define PA_PLOT(DD) plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, ycap)
+#define PA_PLOT(DD)                                                                          \
+  do {                                                                                       \
+    cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                         (int)smem);                                                         \
+    plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, ycap, gstride, rmax);   \
+  } while (0)
   switch (common_degree) {
     case 1: PA_PLOT(1); break;
     case 2: PA_PLOT(2); break;

@@ -60,7 +60,7 @@ def test_static_two_systems_back_to_back(eng):
 
 
 def test_static_rejects_oversized_system(eng):
-    sysm = W.ternary(res=256)   # about 26 MB of workspace
+    sysm = W.ternary(res=512)   # its four 512^3-bit plots alone take 64 MiB
     out = pa.BitArray.empty(sysm.exposed, [sysm.axes[v][2] for v in sysm.exposed])
     with pytest.raises(pa.PaError) as e:
         pa.pa_solve_network_static(sysm.axes, sysm.rels, sysm.exposed, out)
