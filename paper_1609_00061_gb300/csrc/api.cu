@@ -766,7 +766,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<size_t> coeff_off(nrel);
-  int64_t tiles = 0;
+  int64_t tiles = 0, max_tile_words = 1;
   int max_rows = 1, max_deg = 0, common_deg = reqs[0].rel->degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = *reqs[i].rel;
@@ -824,6 +824,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
+    max_tile_words = std::max<int64_t>(max_tile_words, (int64_t)J.rows_per_tile * J.row_words);
     max_deg = std::max(max_deg, r.degree);
     max_res_last = std::max(max_res_last, (int)res_last);
     if (r.degree != common_deg) common_deg = -1;
@@ -853,6 +854,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   op.i1 = max_deg;
   op.i2 = common_deg;
   op.i3 = max_res_last;
+  op.m = max_tile_words;
   bd.ops.push_back(op);
   return plots;
 }
@@ -1012,7 +1014,7 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
     switch (op.kind) {
       case OP_PLOT:
         launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
-                    op.i1, op.i2, op.i3, s);
+                    op.i1, op.i2, op.i3, op.m, s);
         break;
       case OP_MEMSET:
         check_cuda(ctx, cudaMemsetAsync(op.p, 0, (size_t)op.count * 8, s), "cudaMemsetAsync");

@@ -52,7 +52,8 @@ struct PlotJob {
 // degree shared by every job (selects a specialised kernel), or -1 when they
 // differ.
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
-                 int max_degree, int common_degree, int max_res_last, cudaStream_t s);
+                 int max_degree, int common_degree, int max_res_last, int64_t max_tile_words,
+                 cudaStream_t s);
 
 // ------------------------------------------------------------- bit arrays
 // A bit-packed array with `inner` trailing axes flattened into packed rows:

@@ -273,24 +273,31 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   uint64_t* __restrict__ out = J->out;
   constexpr int kG = DS >= 0 ? DS + 1 : kMaxDeg + 1;
   const int nwords = nr * row_words;
-  for (int f = threadIdx.x; f < nwords; f += blockDim.x) {
-    const int r = f / row_words, w = f - r * row_words;
-    const int64_t row = row0 + r;
-    const int i0 = w * 64;
-    const int nb = min(64, res_last - i0);
-    uint64_t word = 0;
-    if (hoisted) {
-      float g[kG];
-      const float* gr = g32s + r * gstride;
+  auto load_g = [&](int r, float* g) {
+    const float* gr = g32s + r * gstride;
 #pragma unroll
-      for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? gr[j] : 0.0f;
-      const float4 th = thrs[r];
-      const float lo = th.x, hi = th.y;
-      uint64_t pending = 0;
-      const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
-      if (nb == 64) {
-        // whole-word test at the middle pixel (see the header)
-        const float yc = ysmem ? ytab_w[32] : ycentre32(ylo, ydelta, i0 + 32);
+    for (int j = 0; j < kG; ++j) g[j] = (DS >= 0 || j <= D) ? gr[j] : 0.0f;
+  };
+  // Phase 1: the whole-word test on every full word (see the header); words it
+  // cannot decide go to a shared list, so that phase 2 evaluates pixels with
+  // every lane busy instead of a few lanes per warp.
+  int* list = reinterpret_cast<int*>(ytab + (ysmem ? res_last + res_last / 64 + 1 : 0));
+  __shared__ int s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < nwords; base += blockDim.x) {
+    const int f = base + threadIdx.x;
+    bool keep = false;
+    if (f < nwords) {
+      keep = true;
+      const int r = f / row_words, w = f - r * row_words;
+      const int i0 = w * 64;
+      if (hoisted && res_last - i0 >= 64) {
+        float g[kG];
+        load_g(r, g);
+        const float4 th = thrs[r];
+        const float yc = ysmem ? ytab[i0 + w + 32] : ycentre32(ylo, ydelta, i0 + 32);
         const float h = J->hword, ya = fabsf(yc), yw = ya + h;
         // Horner for F and F' at y_c; S1 at |y_c| and S2 at |y_c| + h
         float fc = g[D], dc = 0.0f, s1 = 0.0f, s2 = 0.0f;
@@ -303,19 +310,45 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
         const float e1 = (float)(2 * D + 4) * 5.9604645e-8f * s1;  // (2D + 4) 2^-24 S1
         const float taylor = __fmaf_rn(h, fabsf(dc) + e1, 0.5f * h * h * s2) * 1.01f;
         const float margin = __fmaf_rn(4.0f, th.z, taylor);
+        uint64_t* o = out + (row0 + r) * row_words + w;
         if (kind == PA_EQ) {
-          if (fabsf(fc) > hi + margin) {
-            out[row * row_words + w] = 0ull;
-            continue;
+          if (fabsf(fc) > th.y + margin) {
+            *o = 0ull;
+            keep = false;
           }
-        } else if (fc > hi + margin) {
-          out[row * row_words + w] = 0ull;
-          continue;
-        } else if (fc < lo - margin) {
-          out[row * row_words + w] = ~0ull;
-          continue;
+        } else if (fc > th.y + margin) {
+          *o = 0ull;
+          keep = false;
+        } else if (fc < th.x - margin) {
+          *o = ~0ull;
+          keep = false;
         }
       }
+    }
+    // warp-aggregated append of the undecided words
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    int off = 0;
+    if (lane == 0 && m) off = atomicAdd(&s_n, __popc(m));
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (keep) list[off + __popc(m & ((1u << lane) - 1u))] = f;
+  }
+  __syncthreads();
+  // Phase 2: pixel by pixel
+  const int nlist = s_n;
+  for (int e = threadIdx.x; e < nlist; e += blockDim.x) {
+    const int f = list[e];
+    const int r = f / row_words, w = f - r * row_words;
+    const int64_t row = row0 + r;
+    const int i0 = w * 64;
+    const int nb = min(64, res_last - i0);
+    uint64_t word = 0;
+    if (hoisted) {
+      float g[kG];
+      load_g(r, g);
+      const float4 th = thrs[r];
+      const float lo = th.x, hi = th.y;
+      uint64_t pending = 0;
+      const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
       if (kind == PA_EQ) {
         if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
         else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
@@ -343,12 +376,16 @@ cudaError_t probe_kernel_image() {
 }
 
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
-                 int max_degree, int common_degree, int max_res_last, cudaStream_t s) {
+                 int max_degree, int common_degree, int max_res_last, int64_t max_tile_words,
+                 cudaStream_t s) {
   if (total_tiles <= 0) return;
   const int ycap = max_res_last <= kYTabCap ? max_res_last : 0;
   const int gstride = max_degree + 1, rmax = max_rows_per_tile;
+  // thresholds, centre table, then the list of undecided words (one int per
+  // word of the largest tile)
   const size_t smem = plot_thr_offset(rmax, gstride) + (size_t)rmax * 16 +
-                      (size_t)(ycap + ycap / 64 + 1) * sizeof(float);
+                      (size_t)(ycap + ycap / 64 + 1) * sizeof(float) +
+                      (size_t)max_tile_words * sizeof(int);
   const unsigned grid = (unsigned)total_tiles;
 #define PA_PLOT(DD)                                                                          \
   do {                                                                                       \
