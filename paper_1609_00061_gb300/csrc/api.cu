@@ -22,6 +22,12 @@
 #include "pa_internal.h"
 #include "planner.h"
 
+namespace pa {
+namespace {
+struct Memo;
+}
+}  // namespace pa
+
 struct pa_ctx {
   int device = 0;
   size_t cap = 0;
@@ -51,6 +57,10 @@ struct pa_ctx {
   double rate_mma = 4.4e8;     // tensor path (with operand expansion): multiply-adds per microsecond
   std::unordered_map<uint64_t, double> dens_cache;  // relation key -> estimated plot density
   std::unordered_map<uint64_t, double> obs_dens;    // subtree key -> density measured by pa_join_log
+  // the last pa_solve_network program, relaunched without planning when the
+  // next call's arguments and planning state are the same byte for byte
+  uint64_t plan_epoch = 0;  // changes with every setting or measurement that steers planning
+  pa::Memo* memo = nullptr;
 };
 
 namespace pa {
@@ -76,7 +86,7 @@ bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end()
 
 // ------------------------------------------------------------ program
 enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
-              OP_MMA };
+              OP_MMA, OP_CENTRES };
 
 struct Op {
   OpKind kind;
@@ -96,6 +106,7 @@ struct Op {
 const char* op_name(const Op& op) {
   switch (op.kind) {
     case OP_PLOT: return "plot_kernel";
+    case OP_CENTRES: return "plot_centres_kernel";
     case OP_MEMSET: return "memset";
     case OP_RESHAPE:
       return op.rd.mode == kReshapeTranspose ? "reshape_transpose_kernel"
@@ -109,6 +120,15 @@ const char* op_name(const Op& op) {
     default: return "rowor_kernel";
   }
 }
+
+// A planned call kept for reuse: its key (arguments and planning state), its
+// launch list, its descriptor blob (coefficients included) and its statistics.
+struct Memo {
+  std::vector<char> key;
+  std::vector<Op> ops;
+  std::vector<char> blob;
+  pa_stats st{};
+};
 
 // Builds the workspace layout, the descriptor blob and the launch list of a call.
 struct Builder {
@@ -759,14 +779,15 @@ struct PlotReq {
   uint64_t* direct;  // plot straight into this array (pa_plot), else workspace
 };
 
-// Every requested plot in one preparation launch (row polynomials, thresholds,
-// FP32 centre tables) and one plot launch.
+// Every requested plot in two launches: the FP32 centre tables of the last
+// ports (once per distinct axis, not once per block), then the plot itself.
 std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   const int nrel = (int)reqs.size();
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<size_t> coeff_off(nrel);
-  int64_t tiles = 0, max_tile_words = 1;
+  int64_t tiles = 0, max_tile_words = 1, ycen = 0;
+  std::vector<CentreTab> tabs;  // one per distinct last-port axis of the hoisted jobs
   int max_rows = 1, max_deg = 0, common_deg = reqs[0].rel->degree, max_res_last = 1;
   for (int i = 0; i < nrel; ++i) {
     const pa_relation& r = *reqs[i].rel;
@@ -806,6 +827,24 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
     J.nrows = a.nrows();
     J.row_words = a.row_words();
     const int64_t res_last = a.res[a.ndim - 1];
+    if (J.hoisted) {
+      const int a = r.arity - 1;
+      const CentreTab* t = nullptr;
+      for (const CentreTab& c : tabs)
+        if (c.lo == J.lo[a] && c.delta == J.delta[a] && c.res == res_last) t = &c;
+      if (!t) {
+        CentreTab c;
+        c.y32 = reinterpret_cast<float*>(bd.alloc_words((res_last + 1) / 2));
+        c.lo = J.lo[a];
+        c.delta = J.delta[a];
+        c.item0 = ycen;
+        c.res = res_last;
+        ycen += res_last;
+        tabs.push_back(c);
+        t = &tabs.back();
+      }
+      J.y32 = t->y32;
+    }
     {
       const pa_axis& ax = axes[r.vars[r.arity - 1]];
       J.ymax = (float)(fmax(fabs(ax.lo), fabs(ax.hi)) * (1.0 + 0x1p-20));
@@ -845,6 +884,14 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   for (int i = 0; i < nrel; ++i)
     jobs[i].coeffs = reinterpret_cast<const double*>(bd.dev(coeff_off[i]));
   const size_t jobs_off = bd.put(jobs.data(), jobs.size(), 64);
+  if (ycen > 0) {
+    Op cop;
+    cop.kind = OP_CENTRES;
+    cop.off0 = bd.put(tabs.data(), tabs.size(), 64);
+    cop.n = (int)tabs.size();
+    cop.count = ycen;
+    bd.ops.push_back(cop);
+  }
   Op op;
   op.kind = OP_PLOT;
   op.off0 = jobs_off;
@@ -1016,6 +1063,9 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
         launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
                     op.i1, op.i2, op.i3, op.m, s);
         break;
+      case OP_CENTRES:
+        launch_plot_centres(reinterpret_cast<const CentreTab*>(blob + op.off0), op.n, op.count, s);
+        break;
       case OP_MEMSET:
         check_cuda(ctx, cudaMemsetAsync(op.p, 0, (size_t)op.count * 8, s), "cudaMemsetAsync");
         break;
@@ -1111,7 +1161,8 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Size, build and run one call on the context's arena.
 template <class F>
-pa_status run_call(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body) {
+pa_status run_call(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body,
+                   std::vector<char>* memo_key = nullptr) {
   try {
     if (cudaSetDevice(ctx->device) != cudaSuccess) {
       cudaGetLastError();
@@ -1133,6 +1184,83 @@ pa_status run_call(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body) {
     bd.st.workspace_bytes = (int64_t)bd.used;
     bd.st.n_launches = (int32_t)bd.ops.size();
     if (stats) *stats = bd.st;
+    if (memo_key) {
+      if (!ctx->memo) ctx->memo = new Memo();
+      Memo& m = *ctx->memo;
+      m.key.swap(*memo_key);
+      m.ops = std::move(bd.ops);
+      m.blob = std::move(bd.blob);
+      m.st = bd.st;
+    }
+    return PA_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+template <class T>
+void put_val(std::vector<char>& k, const T& v) {
+  const char* p = reinterpret_cast<const char*>(&v);
+  k.insert(k.end(), p, p + sizeof v);
+}
+void put_bytes(std::vector<char>& k, const void* p, size_t n) {
+  const char* c = static_cast<const char*>(p);
+  k.insert(k.end(), c, c + n);
+}
+
+// Everything a validated pa_solve_network call's program depends on: each
+// argument by value (coefficients included), the stream, and the context
+// state that steers planning or is written into the program.
+std::vector<char> solve_key(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,
+                            const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
+                            const pa_options* opts, const pa_array* out, void* stream) {
+  std::vector<char> k;
+  k.reserve(512);
+  put_val(k, ctx->plan_epoch);
+  put_val(k, reinterpret_cast<uintptr_t>(ctx->arena));
+  put_val(k, ctx->prof);
+  put_val(k, reinterpret_cast<uintptr_t>(stream));
+  put_val(k, nvars);
+  for (int i = 0; i < nvars; ++i) {
+    put_val(k, axes[i].lo);
+    put_val(k, axes[i].hi);
+    put_val(k, axes[i].res);
+  }
+  put_val(k, nrel);
+  for (int i = 0; i < nrel; ++i) {
+    const pa_relation& r = rels[i];
+    put_val(k, r.arity);
+    put_bytes(k, r.vars, sizeof(int32_t) * r.arity);
+    put_val(k, r.degree);
+    put_val(k, r.kind);
+    put_val(k, r.eps);
+    put_bytes(k, r.coeffs, sizeof(double) * coeff_count(r.arity, r.degree));
+  }
+  put_val(k, nexposed);
+  put_bytes(k, exposed, sizeof(int32_t) * nexposed);
+  put_val(k, opts ? opts->strict : 0);
+  put_val(k, opts ? opts->order : 0);
+  if (opts && opts->order == PA_ORDER_GIVEN) {
+    put_val(k, opts->npairs);
+    put_bytes(k, opts->pairs, sizeof(int32_t) * 2 * opts->npairs);
+  }
+  put_val(k, reinterpret_cast<uintptr_t>(out->words));
+  return k;
+}
+
+// Relaunch the kept program.  Its blob is uploaded again like any call's: the
+// coefficients are host inputs of every call, and another call may have
+// replaced the blob region of the arena since.
+pa_status run_memo(pa_ctx* ctx, cudaStream_t s, pa_stats* stats) {
+  try {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, PA_ERR_CUDA, "cudaSetDevice failed");
+    }
+    Memo& m = *ctx->memo;
+    upload_blob(ctx, m.blob, s);
+    run_ops(ctx, m.ops, ctx->arena, s, ctx->prof);
+    if (stats) *stats = m.st;
     return PA_OK;
   } catch (const Fail& f) {
     return f.st;
@@ -1543,6 +1671,7 @@ void pa_destroy(pa_ctx* ctx) {
   if (ctx->d_stat) cudaFree(ctx->d_stat);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+  delete ctx->memo;
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -1554,6 +1683,7 @@ pa_status pa_set_contract_path(pa_ctx* ctx, int32_t path) {
   if (path != PA_PATH_AUTO && path != PA_PATH_ROWOR && path != PA_PATH_MMA)
     return set_err(ctx, PA_ERR_INVALID_ARG, "contract path must be PA_PATH_AUTO, _ROWOR or _MMA");
   ctx->path = path;
+  ctx->plan_epoch++;
   return PA_OK;
 }
 
@@ -1573,6 +1703,7 @@ pa_status pa_set_rates(pa_ctx* ctx, const pa_rates* r) {
   ctx->rate_or = r->rowor_words_per_us;
   ctx->rate_or_dense = r->rowor_words_per_us_dense;
   ctx->rate_mma = r->mma_macs_per_us;
+  ctx->plan_epoch++;
   return PA_OK;
 }
 
@@ -1704,6 +1835,7 @@ pa_status pa_autotune(pa_ctx* ctx, pa_rates* out, void* stream) {
     ctx->rate_or = rate_or[0];
     ctx->rate_or_dense = rate_or[1];
     ctx->rate_mma = (double)R * R * R / t_mma;
+    ctx->plan_epoch++;
   } while (false);
   if (st == PA_OK && out) pa_get_rates(ctx, out);
   if (e0) cudaEventDestroy(e0);
@@ -1879,10 +2011,18 @@ pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int3
   } catch (const Fail& f) {
     return f.st;
   }
+  // a learned order depends on a model that may change between calls: never kept
+  const bool keep = !(opts && opts->order == PA_ORDER_LEARNED);
+  std::vector<char> key;
+  if (keep) {
+    key = solve_key(ctx, nvars, axes, nrel, rels, nexposed, exposed, opts, out, stream);
+    if (ctx->memo && ctx->memo->key == key)
+      return run_memo(ctx, static_cast<cudaStream_t>(stream), stats);
+  }
   pa_status st = resolve_learned(ctx, opts, nets);
   if (st != PA_OK) return st;
   return run_call(ctx, static_cast<cudaStream_t>(stream), stats,
-                  [&](Builder& bd) { build_networks(bd, nets); });
+                  [&](Builder& bd) { build_networks(bd, nets); }, keep ? &key : nullptr);
 }
 
 static pa_status check_batch(pa_ctx* ctx, int32_t nsys, const pa_system* systems, pa_array* outs,
@@ -2200,6 +2340,7 @@ pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts,
     // remember the measured densities for later path choices on these relations
     const Network& n0 = nets[0];
     if ((int)n0.slot_keys.size() == n0.nrel + nj) {
+      ctx->plan_epoch++;
       if (ctx->obs_dens.size() >= (1u << 16)) ctx->obs_dens.clear();
       for (int t = 0; t < nj; ++t)
         ctx->obs_dens[n0.slot_keys[n0.nrel + t]] =

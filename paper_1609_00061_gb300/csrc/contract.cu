@@ -309,20 +309,37 @@ void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows,
 // ---------------------------------------------------------------- row-OR
 // One CTA owns the tile B[b][k0 .. k0+Kc)[n0 .. n0+Nt) in shared memory, staged
 // by the Tensor Memory Accelerator (2-D boxes of 256 rows x Nt words) when the
-// row pitch allows it, else by plain loads, followed by an all-zero sentinel
-// row.  Each warp then takes one output row at a time:
-//   1. its lanes load up to 32 words of the row's A bits for this K range,
-//      count their set bits and prefix-sum the counts across the warp;
-//   2. every lane writes the tile-row indices of its set bits into the warp's
-//      list in shared memory (bits past the tile point at the sentinel);
-//   3. the warp splits into 32/Nt groups of Nt lanes; group g ORs tile rows
+// row pitch allows it, else by plain loads.  Next to it the CTA builds the ORs
+// of aligned blocks of 4, 16 and 64 tile rows (tables T2, T4, T6; T0 is the
+// tile itself), plus an all-zero sentinel row.  A run of set bits in a row of
+// A selects a run of B rows, whose OR is the OR of the maximal aligned blocks
+// covering it: the plotted relations are thick curves, so most set bits lie in
+// long runs and a row needs a few block lookups instead of one per bit.
+// Each warp then takes one output row at a time:
+//   1. its lanes load up to 32 words of the row's A bits for this K range and
+//      split each word into maximal all-ones aligned blocks of 64, 16, 4 and 1
+//      bits (a few bit operations), counting them;
+//   2. every lane writes the table rows of its blocks into the warp's list in
+//      shared memory;
+//   3. the warp splits into 32/Nt groups of Nt lanes; group g ORs table rows
 //      list[g], list[g + 32/Nt], ... (four loads in flight per lane), lane l of
 //      a group holding word n0 + l;
 //   4. the groups' words are OR-ed together with shuffles and stored.
 namespace {
 
-constexpr int kRowOrThreads = 512;
-constexpr int kListCap = 32 * 64 + 128;  // one batch of 32 A words, plus sentinel padding
+constexpr int kRowOrThreads = 1024;
+// Entries of a warp's list per window, plus sentinel padding.  A unit whose
+// blocks do not fit is processed in several windows.
+constexpr int kListWin = 256;
+constexpr int kListCap = kListWin + 128;
+
+// Tile rows of the tables for a K range staged in `staged` rows: T0 (rounded
+// up to whole 64-row groups), the sentinel, T2, T4 and T6.
+__host__ __device__ __forceinline__ int64_t rowor_r64(int64_t staged) { return (staged + 63) / 64 * 64; }
+__host__ __device__ __forceinline__ int64_t rowor_table_rows(int64_t staged) {
+  const int64_t r64 = rowor_r64(staged);
+  return r64 + 1 + r64 / 4 + r64 / 16 + r64 / 64;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -355,6 +372,9 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
   extern __shared__ __align__(1024) uint64_t bs[];
   __shared__ RowOrDesc sd;
   __shared__ int s_p;
+  // the next launch may be scheduled onto SMs this grid frees; it waits for
+  // this grid's completion before it touches any data
+  asm volatile("griddepcontrol.launch_dependents;");
   const int tid = threadIdx.x;
   const int nwarps = blockDim.x >> 5;
   if (tid == 0) {
@@ -371,7 +391,9 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
   const RowOrDesc& d = sd;
   const CUtensorMap* tmap = maps + p;
   const int64_t staged = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
-  uint16_t* lists = reinterpret_cast<uint16_t*>(bs + (staged + 1) * G);
+  const int r64 = (int)rowor_r64(staged);
+  const int sent = r64, t2 = r64 + 1, t4 = t2 + r64 / 4, t6 = t4 + r64 / 16;
+  uint16_t* lists = reinterpret_cast<uint16_t*>(bs + rowor_table_rows(staged) * G);
   uint64_t* bar = reinterpret_cast<uint64_t*>(lists + (size_t)nwarps * kListCap);
 
   int64_t cta = (int64_t)blockIdx.x - cta0s[p];
@@ -395,6 +417,9 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
       // the tensor map was written to global memory by a copy before the launch
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
     }
+    // everything the earlier kernels of the stream wrote (A, B) is complete
+    // and visible past this point, and C may be overwritten
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)nbox * 256u * (uint32_t)G * 8u;
@@ -417,14 +442,32 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
       return;
     }
   } else {
-    for (int idx = tid; idx < kc_len * G; idx += blockDim.x) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // rows past the K range are zero (only block tables that no lookup reads
+    // include them)
+    for (int idx = tid; idx < r64 * G; idx += blockDim.x) {
       const int r = idx / G, c = idx % G;
       const int64_t n = n0 + c;
-      bs[idx] = (n < d.Nw) ? __ldg(d.B + (b * d.K + k0 + r) * d.Nw + n) : 0ull;
+      bs[idx] = (r < kc_len && n < d.Nw) ? __ldg(d.B + (b * d.K + k0 + r) * d.Nw + n) : 0ull;
     }
   }
-  if (tid < G) bs[(size_t)kc_len * G + tid] = 0ull;  // sentinel row
+  if (tid < G) bs[(size_t)sent * G + tid] = 0ull;  // sentinel row
   __syncthreads();
+  // block tables: each row the OR of four rows of the level below
+  {
+    const int lv_src[3] = {0, t2, t4}, lv_dst[3] = {t2, t4, t6}, lv_n[3] = {r64 / 4, r64 / 16, r64 / 64};
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const uint64_t* src = bs + (size_t)lv_src[l] * G;
+      uint64_t* dst = bs + (size_t)lv_dst[l] * G;
+      for (int idx = tid; idx < lv_n[l] * G; idx += blockDim.x) {
+        const int q = idx / G, c = idx - (idx / G) * G;
+        const uint64_t* s0 = src + (size_t)(4 * q) * G + c;
+        dst[idx] = s0[0] | s0[G] | s0[2 * G] | s0[3 * G];
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- output rows, one warp each
   const int warp = tid >> 5, lane = tid & 31;
@@ -445,9 +488,6 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
   const int nunits = nrows_w * nbat;
   const uint64_t* __restrict__ abase = d.A + (b * d.M) * d.a_row_words;
   const int64_t arw = d.a_row_words;
-  int* wcount = reinterpret_cast<int*>(bar + 1) + warp;
-  if (lane == 0) *wcount = 0;
-  __syncwarp();
   auto load_unit = [&](int u) -> uint64_t {
     if (u >= nunits) return 0ull;
     const int i = (nbat == 1) ? u : u / nbat;
@@ -467,32 +507,65 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
     const int q = u - i * nbat;
     if (q == 0) acc = 0;
     if (__any_sync(0xffffffffu, a != 0ull)) {
-      // list of the set bits (tile-row indices), in any order
-      const int c = __popcll(a);
-      int off = c ? atomicAdd(wcount, c) : 0;
+      // tile row of this word's bit 0 (a multiple of 64); bits past the K
+      // range are dropped
       const int base = (kw0 + q * 32 + lane) * 64 - (int)k0;
-      while (a) {
-        const int bit = __ffsll((long long)a) - 1;
-        a &= a - 1;
-        const int ix = base + bit;
-        list[off++] = (uint16_t)(ix < kc_len ? ix : kc_len);
+      if (base + 64 > kc_len) a &= (base >= kc_len) ? 0ull : ((1ull << (kc_len - base)) - 1ull);
+      // maximal all-ones aligned blocks of the word: bit 4i of f4 when bits
+      // 4i..4i+3 are set, bit 16i of f16 when bits 16i..16i+15 are set, f1 the
+      // set bits in neither; a full word is one 64-block
+      const bool full = (a == ~0ull);
+      uint64_t f16 = 0, f4 = 0, f1 = a;
+      if (!full) {
+        uint64_t t = a & (a >> 1);
+        t &= t >> 2;
+        f4 = t & 0x1111111111111111ull;
+        uint64_t u4 = f4 & (f4 >> 4);
+        u4 &= u4 >> 8;
+        f16 = u4 & 0x0001000100010001ull;
+        const uint64_t m16 = f16 * 0xFFFFull;
+        f4 &= ~m16;
+        f1 = a & ~(m16 | f4 * 0xFull);
       }
-      __syncwarp();
-      const int T = *wcount;
-      // pad to a whole number of rounds with the sentinel row (4P entries,
-      // which is more than one per lane when the groups are narrow)
-      for (int t = lane; t < 4 * P; t += 32) list[T + t] = (uint16_t)kc_len;
-      __syncwarp();
-      for (int e = grp; e < T; e += 4 * P) {
-        const int i0 = list[e], i1 = list[e + P], i2 = list[e + 2 * P], i3 = list[e + 3 * P];
-        acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
+      const int c = full ? 1 : __popcll(f16) + __popcll(f4) + __popcll(f1);
+      // this lane's entries are [o, o + c) of the unit's T, in a fixed order
+      int o = c;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, o, sh);
+        if (lane >= sh) o += v;
       }
-      __syncwarp();
-      if (lane == 0) {
-        *wcount = 0;
-        if (d.stat) atomicAdd(d.stat, (unsigned long long)T * G);
+      const int T = __shfl_sync(0xffffffffu, o, 31);
+      o -= c;
+      if (d.stat && lane == 0) atomicAdd(d.stat, (unsigned long long)T * G);
+      for (int w0 = 0; w0 < T; w0 += kListWin) {
+        const int w1 = min(T, w0 + kListWin);
+        if (o < w1 && o + c > w0) {
+          // write the entries with index in [w0, w1)
+          int e = o;
+          auto put = [&](int row) {
+            if (e >= w0 && e < w1) list[e - w0] = (uint16_t)row;
+            ++e;
+          };
+          if (full) {
+            put(t6 + base / 64);
+          } else {
+            for (uint64_t m = f16; m; m &= m - 1) put(t4 + (base + __ffsll((long long)m) - 1) / 16);
+            for (uint64_t m = f4; m; m &= m - 1) put(t2 + (base + __ffsll((long long)m) - 1) / 4);
+            for (uint64_t m = f1; m; m &= m - 1) put(base + __ffsll((long long)m) - 1);
+          }
+        }
+        // pad to a whole number of rounds with the sentinel row (4P entries,
+        // which is more than one per lane when the groups are narrow)
+        const int n = w1 - w0;
+        for (int t = lane; t < 4 * P; t += 32) list[n + t] = (uint16_t)sent;
+        __syncwarp();
+        for (int e = grp; e < n; e += 4 * P) {
+          const int i0 = list[e], i1 = list[e + P], i2 = list[e + 2 * P], i3 = list[e + 3 * P];
+          acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (q == nbat - 1) {
       uint64_t r = acc;
@@ -533,29 +606,37 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-constexpr size_t kTileBudget = 156 * 1024;  // shared bytes for one B tile (the lists take 68 KB more)
+// Shared memory of one CTA: the tables plus the warps' lists, their counters
+// and the mbarrier, within the 227 KB a CTA may opt into.
+constexpr size_t kSmemLimit = 227 * 1024 - 2048;  // the kernel's static shared memory stays out
+constexpr size_t kListBytes = (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16 +
+                              (size_t)(kRowOrThreads / 32) * 4;
+
+size_t table_bytes(int64_t staged, int Nt) { return (size_t)rowor_table_rows(staged) * Nt * 8; }
 
 }  // namespace
 
 EncodeTiledFn tensor_map_encoder() { return encode_fn(); }
 
 void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
-  // widest power-of-two tile (<= 32 words, <= the row) whose K range fits the budget
+  const bool tma_ok = (d.Nw % 2 == 0) && (reinterpret_cast<uintptr_t>(d.B) % 16 == 0) &&
+                      (d.nbatch * d.K < (1ll << 31)) && encode_fn() != nullptr;
+  auto staged_of = [&](int64_t kc, bool tma) { return tma ? (kc + 255) / 256 * 256 : kc; };
+  // widest power-of-two tile (<= 32 words, <= the row) whose whole K range fits
   int nt_max = 1;
   while (nt_max < 32 && nt_max < d.Nw) nt_max <<= 1;
   int Nt = nt_max;
-  while (Nt > 2 && (size_t)(d.K + 1) * Nt * 8 > kTileBudget) Nt >>= 1;
+  while (Nt > 2 && table_bytes(staged_of(d.K, tma_ok && Nt % 2 == 0), Nt) + kListBytes > kSmemLimit)
+    Nt >>= 1;
   d.Nt = Nt;
-  int64_t kc = (int64_t)(kTileBudget / ((size_t)Nt * 8)) - 1;
-  const bool tma_ok = (d.Nw % 2 == 0) && (Nt % 2 == 0) &&
-                      (reinterpret_cast<uintptr_t>(d.B) % 16 == 0) &&
-                      (d.nbatch * d.K < (1ll << 31)) && encode_fn() != nullptr;
-  d.use_tma = tma_ok ? 1 : 0;
-  if (tma_ok) {
-    // the staged rows are whole 256-row boxes, plus the sentinel row
-    d.Kc = (int32_t)(((d.K + 255) / 256 * 256 <= kc) ? d.K : std::max<int64_t>(256, kc / 256 * 256));
+  d.use_tma = (tma_ok && Nt % 2 == 0) ? 1 : 0;
+  const int64_t step = d.use_tma ? 256 : 64;
+  if (table_bytes(staged_of(d.K, d.use_tma), Nt) + kListBytes <= kSmemLimit) {
+    d.Kc = (int32_t)d.K;
   } else {
-    d.Kc = (int32_t)((d.K <= kc) ? d.K : std::max<int64_t>(64, kc / 64 * 64));
+    int64_t kc = step;
+    while (table_bytes(kc + step, Nt) + kListBytes <= kSmemLimit) kc += step;
+    d.Kc = (int32_t)kc;
   }
   d.n_tiles = (d.Nw + Nt - 1) / Nt;
   d.k_chunks = (d.K + d.Kc - 1) / d.Kc;
@@ -571,9 +652,8 @@ void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
 }
 
 size_t rowor_smem_bytes(const RowOrDesc& d) {
-  const int64_t rows = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
-  return (size_t)(rows + 1) * d.Nt * 8 + (size_t)(kRowOrThreads / 32) * kListCap * 2 + 16 +
-         (size_t)(kRowOrThreads / 32) * 4;
+  const int64_t staged = d.use_tma ? ((int64_t)d.Kc + 255) / 256 * 256 : d.Kc;
+  return table_bytes(staged, d.Nt) + kListBytes;
 }
 
 int64_t rowor_ctas(const RowOrDesc& d) { return d.nbatch * d.n_tiles * d.k_chunks * d.row_splits; }
@@ -597,12 +677,23 @@ cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
                          cudaStream_t s) {
   if (nprob <= 0 || grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  // programmatic dependent launch: CTAs may start on SMs the previous kernel
+  // has left and set up while it finishes (the kernel waits before any data)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kRowOrThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
 #define PA_ROWOR(GG)                                                                         \
   do {                                                                                       \
     cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                          (int)smem);                                                         \
-    rowor_tile_kernel<GG><<<(unsigned)grid, kRowOrThreads, smem, s>>>(d_descs, d_maps, d_cta0, \
-                                                                     nprob);                 \
+    cudaLaunchKernelEx(&cfg, rowor_tile_kernel<GG>, d_descs, d_maps, d_cta0, nprob);         \
   } while (0)
   switch (Nt) {
     case 1: PA_ROWOR(1); break;

@@ -29,6 +29,7 @@ struct PlotJob {
   uint64_t* out;                    // device, pa_array layout
   double lo[kMaxDim];               // per port: range start of its variable
   double delta[kMaxDim];            // per port: pixel width of its variable
+  const float* y32;                 // [res_last] FP32 centres of the last port (hoisted jobs)
   int64_t nrows;                    // rows = product of all but the last array axis
   int64_t row_words;                // ceil(res_last / 64)
   int64_t tile0;                    // first block of this job in the plot launch
@@ -47,6 +48,18 @@ struct PlotJob {
   int32_t block_off[kMaxDeg + 1];   // nest-order offset of the coefficients with e_last = j
 };
 
+// One FP32 centre table: y32[i] = fl32(lo + (i + 1/2) delta) for i < res, the
+// last-port centres shared by every hoisted plot job over that axis.
+struct CentreTab {
+  float* y32;
+  double lo, delta;
+  int64_t item0;  // first item of this table in the centre-table launch
+  int64_t res;
+};
+// Every table in one launch (one thread per centre), before the plot launch;
+// the plot kernel waits for it only after its row set-up (programmatic
+// dependent launch), so the two overlap.
+void launch_plot_centres(const CentreTab* d_tabs, int ntabs, int64_t total_items, cudaStream_t s);
 // One launch plots every job: blocks of rows_per_tile rows, each computing its
 // rows' polynomials and thresholds in shared memory first.  common_degree: the
 // degree shared by every job (selects a specialised kernel), or -1 when they

@@ -45,21 +45,10 @@
 namespace pa {
 
 // -------------------------------------------------------- nested evaluation
-// sum_{e_k = 0}^{rem} nest(k-1, rem - e_k) * x_k^{e_k}; coefficients are read
-// in nest order through cp.
-__device__ double nest_dev(int k, int rem, const double*& cp, const double* x) {
-  if (k < 0) return *cp++;
-  double s = 0.0, pw = 1.0;
-  for (int e = 0; e <= rem; ++e) {
-    const double term = __dmul_rn(nest_dev(k - 1, rem - e, cp, x), pw);
-    s = (e == 0) ? term : __dadd_rn(s, term);
-    pw = __dmul_rn(pw, x[k]);
-  }
-  return s;
-}
-
-// The same sum with the depth known at compile time (no call stack): used for
-// the row polynomials, K = arity - 2.
+// nest(k, rem) = sum_{e_k = 0}^{rem} nest(k-1, rem - e_k) * x_k^{e_k}, with
+// nest(-1, .) the next coefficient in nest order (read through cp).  No
+// evaluation recurses at run time: a recursive device function runs on the
+// 1 KB default call stack, which an 8-port relation (eight frames) overflows.
 template <int K>
 __device__ __forceinline__ double nest_t(int rem, const double*& cp, const double* x) {
   if constexpr (K < 0) {
@@ -75,13 +64,57 @@ __device__ __forceinline__ double nest_t(int rem, const double*& cp, const doubl
   }
 }
 
+struct NestOut {
+  double v;
+  const double* cp;  // past the coefficients read
+};
+
+// Any depth as a loop over an explicit per-depth state (partial sum, power of
+// x_L, exponent, remaining degree): the same products and sums in the same
+// order as nest_t, out of line and with few registers, for the deep cases.
+__device__ __noinline__ NestOut nest_deep(int k, int rem, const double* cp, const double* x) {
+  if (k < 0) return {*cp, cp + 1};
+  double s[kMaxDim], pw[kMaxDim];
+  int e[kMaxDim], rm[kMaxDim];
+  int L = k;
+  rm[k] = rem;
+  e[k] = 0;
+  pw[k] = 1.0;
+  s[k] = 0.0;
+  for (;;) {
+    // open the term e[L] of depth L down to depth 0
+    while (L > 0) {
+      rm[L - 1] = rm[L] - e[L];
+      e[L - 1] = 0;
+      pw[L - 1] = 1.0;
+      s[L - 1] = 0.0;
+      --L;
+    }
+    double v = *cp++;  // nest(-1, .): the next coefficient
+    // close terms upward while depths complete
+    for (;;) {
+      const double term = __dmul_rn(v, pw[L]);
+      s[L] = (e[L] == 0) ? term : __dadd_rn(s[L], term);
+      pw[L] = __dmul_rn(pw[L], x[L]);
+      if (++e[L] <= rm[L]) break;
+      if (L == k) return {s[k], cp};
+      v = s[L];
+      ++L;
+    }
+  }
+}
+
 __device__ __forceinline__ double nest_rows(int k, int rem, const double*& cp, const double* x) {
   switch (k) {
     case -1: return nest_t<-1>(rem, cp, x);
     case 0: return nest_t<0>(rem, cp, x);
     case 1: return nest_t<1>(rem, cp, x);
     case 2: return nest_t<2>(rem, cp, x);
-    default: return nest_dev(k, rem, cp, x);
+    default: {
+      const NestOut o = nest_deep(k, rem, cp, x);
+      cp = o.cp;
+      return o.v;
+    }
   }
 }
 
@@ -123,7 +156,7 @@ __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i)
   double x[kMaxDim];
   for (int p = 0; p < J->arity; ++p) x[p] = centre(J->lo[p], J->delta[p], idx[J->port_axis[p]]);
   const double* cp = J->coeffs;
-  return decide64(nest_dev(J->arity - 1, J->degree, cp, x), J->kind, J->eps, J->strict);
+  return decide64(nest_rows(J->arity - 1, J->degree, cp, x), J->kind, J->eps, J->strict);
 }
 
 // --------------------------------------------------------------- plot kernel
@@ -147,20 +180,45 @@ __host__ __device__ __forceinline__ size_t plot_thr_offset(int rmax, int gstride
 
 // The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
 // certainly on, bit b of *pending when only the FP64 evaluation can decide.
-// The FP32 centre of last-axis pixel i (the table entry when staged).
+// The FP32 centre of last-axis pixel i.
 __device__ __forceinline__ float ycentre32(double ylo, double ydelta, int i) {
   return __double2float_rn(centre(ylo, ydelta, i));
 }
 
+// Centre tables, one thread per centre.  The plot launch that follows may
+// start as soon as every block of this one has begun.
+__global__ void __launch_bounds__(256)
+plot_centres_kernel(const CentreTab* __restrict__ tabs, int ntabs, int64_t total) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ntabs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tabs[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const CentreTab& T = tabs[lo];
+    const int i = (int)(it - T.item0);
+    T.y32[i] = ycentre32(T.lo, T.delta, i);
+  }
+}
+
+void launch_plot_centres(const CentreTab* d_tabs, int ntabs, int64_t total_items, cudaStream_t s) {
+  if (total_items <= 0) return;
+  int64_t blocks = (total_items + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  plot_centres_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_tabs, ntabs, total_items);
+}
+
 template <int DS, bool EQ, bool YS, bool FULL>
 __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
-                                          const float* ytab_w, double ylo, double ydelta, int i0,
-                                          int nb, uint64_t* on, uint64_t* pending) {
+                                          const float* ytab_w, const float* __restrict__ y32g,
+                                          int i0, int nb, uint64_t* on, uint64_t* pending) {
   uint32_t on_lo = 0, on_hi = 0, pe_lo = 0, pe_hi = 0;
 #pragma unroll
   for (int bb = 0; bb < 64; ++bb) {
     if (FULL || bb < nb) {
-      const float y = YS ? ytab_w[bb] : ycentre32(ylo, ydelta, i0 + bb);
+      const float y = YS ? ytab_w[bb] : __ldg(y32g + i0 + bb);
       float s = g[0], pw = y;
       if (DS >= 0) {
 #pragma unroll
@@ -192,16 +250,17 @@ __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float
 
 template <int DS, bool EQ, bool YS>
 __device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, float hi,
-                                              const float* ytab_w, double ylo, double ydelta,
-                                              int i0, int nb, uint64_t* on, uint64_t* pending) {
-  if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, on, pending);
-  else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, on, pending);
+                                              const float* ytab_w, const float* y32g, int i0,
+                                              int nb, uint64_t* on, uint64_t* pending) {
+  if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, y32g, i0, nb, on, pending);
+  else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, y32g, i0, nb, on, pending);
 }
 
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
 plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstride, int rmax) {
   extern __shared__ __align__(16) unsigned char plot_smem[];
+  asm volatile("griddepcontrol.launch_dependents;");
   // [rmax][gstride] FP64 row polynomials, [rmax][gstride] FP32 copies,
   // [rmax] thresholds, then the padded FP32 centre table
   double* g64s = reinterpret_cast<double*>(plot_smem);
@@ -233,9 +292,6 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
     // set-up: the centre table, and per row (one thread each) the row
     // polynomial g_0..g_D in FP64 (the inner nested sums of the pa.h order),
     // its FP32 copy and the row's thresholds eps -+ B_row
-    if (ysmem)
-      for (int i = threadIdx.x; i < res_last; i += blockDim.x)
-        ytab[ypad(i)] = ycentre32(ylo, ydelta, i);
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
       int64_t rest = row0 + r;
       int64_t idx[kMaxDim];
@@ -266,6 +322,14 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
       }
       thrs[r] = make_float4(tlo, thi, B, 0.0f);
     }
+  }
+  // the centre tables (and any earlier work in the stream) are complete and
+  // visible past this point; nothing global is read or written before it but
+  // the job descriptors and coefficients
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (hoisted) {
+    if (ysmem)
+      for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = J->y32[i];
     __syncthreads();
   }
   const int kind = J->kind, strict = J->strict;
@@ -297,7 +361,7 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
         float g[kG];
         load_g(r, g);
         const float4 th = thrs[r];
-        const float yc = ysmem ? ytab[i0 + w + 32] : ycentre32(ylo, ydelta, i0 + 32);
+        const float yc = ysmem ? ytab[i0 + w + 32] : __ldg(J->y32 + i0 + 32);
         const float h = J->hword, ya = fabsf(yc), yw = ya + h;
         // Horner for F and F' at y_c; S1 at |y_c| and S2 at |y_c| + h
         float fc = g[D], dc = 0.0f, s1 = 0.0f, s2 = 0.0f;
@@ -350,11 +414,11 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
       uint64_t pending = 0;
       const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
       if (kind == PA_EQ) {
-        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
-        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
+        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
       } else {
-        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
-        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, ylo, ydelta, i0, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
+        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
       }
       while (pending) {
         const int bb = __ffsll((long long)pending) - 1;
@@ -387,11 +451,23 @@ void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_
                       (size_t)(ycap + ycap / 64 + 1) * sizeof(float) +
                       (size_t)max_tile_words * sizeof(int);
   const unsigned grid = (unsigned)total_tiles;
+  // programmatic dependent launch: the blocks may start while the centre
+  // tables are being computed and wait for them after their row set-up
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kPlotThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
 #define PA_PLOT(DD)                                                                          \
   do {                                                                                       \
     cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                          (int)smem);                                                         \
-    plot_kernel<DD><<<grid, kPlotThreads, smem, s>>>(d_jobs, njobs, ycap, gstride, rmax);   \
+    cudaLaunchKernelEx(&cfg, plot_kernel<DD>, d_jobs, njobs, ycap, gstride, rmax);           \
   } while (0)
   switch (common_degree) {
     case 1: PA_PLOT(1); break;

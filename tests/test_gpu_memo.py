@@ -1,0 +1,99 @@
+"""GPU parity of repeated pa_solve_network calls: a call whose arguments and
+planning state equal the previous call's relaunches the kept program without
+planning.  Whatever changes in between (coefficients in place, another call that
+replaces the uploaded descriptors, the contraction path, the output buffer), the
+bits stay equal to the oracle's."""
+import numpy as np
+import pytest
+
+import paper_1609_00061_gb300 as pa
+from paper_1609_00061_gb300 import workloads as W
+
+from test_gpu_parity import check_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    e = pa.Engine(0)
+    yield e
+    e.close()
+
+
+def solve_into(eng, sysm, out):
+    st = pa.pa_solve_network(eng.ctx, sysm.axes, sysm.rels, sysm.exposed, out)
+    eng.sync()
+    return st
+
+
+def fresh_out(sysm):
+    return pa.BitArray.empty(sysm.exposed, [sysm.axes[v][2] for v in sysm.exposed], 0)
+
+
+def test_repeat_and_change_in_place(eng, orc):
+    sysm = W.chain(res=300, nrel=5, seed=71)
+    out = fresh_out(sysm)
+    want = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
+    st1 = solve_into(eng, sysm, out)
+    check_same(out, want, "first call")
+    out.words.zero_()
+    st2 = solve_into(eng, sysm, out)  # same arguments: the kept program runs again
+    check_same(out, want, "repeated call")
+    assert st1 == st2
+    # new coefficient values in the same arrays: a different program
+    for r in sysm.rels:
+        r.coeffs[:] = r.coeffs * -1.0 + 0.125
+    want2 = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
+    assert (want2 != want).any()
+    solve_into(eng, sysm, out)
+    check_same(out, want2, "coefficients changed in place")
+
+
+def test_other_calls_in_between(eng, orc):
+    sysm = W.chain(res=257, nrel=4, seed=72)
+    other = W.circle_parabola(res=200)
+    out, out_o = fresh_out(sysm), fresh_out(other)
+    want = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
+    want_o = orc.solve(other.axes, other.rels, other.exposed).data
+    for k in range(3):
+        out.words.zero_()
+        solve_into(eng, sysm, out)
+        check_same(out, want, f"system, round {k}")
+        # another solve, a plot and a contraction replace the uploaded descriptors
+        solve_into(eng, other, out_o)
+        check_same(out_o, want_o, f"other system, round {k}")
+        eng.plot(sysm.rels[0], sysm.axes)
+        eng.sync()
+    out.words.zero_()
+    solve_into(eng, sysm, out)
+    solve_into(eng, sysm, out)
+    check_same(out, want, "after the interleaved calls")
+
+
+def test_path_and_output_changes(eng, orc):
+    sysm = W.chain(res=512, nrel=4, seed=73)
+    want = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
+    outs = [fresh_out(sysm) for _ in range(2)]
+    for path in ("rowor", "mma", "auto"):
+        eng.set_path(path)
+        for o in outs:
+            o.words.zero_()
+            solve_into(eng, sysm, o)
+            solve_into(eng, sysm, o)
+            check_same(o, want, f"path {path}")
+    eng.set_path("auto")
+
+
+def test_learned_order_not_kept(eng, orc):
+    sysm = W.chain(res=200, nrel=5, seed=74)
+    want = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
+    m = pa.CostModel(eng, hidden=32, nlayers=2)
+    for _ in range(2):
+        out, _ = eng.solve(sysm, order="learned", model=m)
+        eng.sync()
+        check_same(out, want, "learned order")
+    m.close()

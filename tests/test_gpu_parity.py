@@ -108,6 +108,29 @@ def test_plot_repeated_variable(eng, orc):
         check_same(eng.plot(rel, axes), diag.data, str(vs))
 
 
+@pytest.mark.parametrize("vs,degree", [((0, 1, 2, 0, 1, 2, 0, 1), 3), ((2, 0, 1, 2), 4),
+                                       ((0, 1, 2, 3, 4, 5, 6), 3), ((0, 1, 2, 3, 4, 5, 6, 7), 2)])
+def test_plot_deep_nesting(eng, orc, vs, degree):
+    """Seven and eight ports: the nested FP64 sums of the pa.h evaluation order at
+    depths 5 to 7, on the row path (distinct variables) and the per-pixel path
+    (repeated ones)."""
+    rng = W.SplitMix64(3100 + len(vs) + 10 * degree)
+    nv = max(vs) + 1
+    axes = [(-1.2 - 0.05 * v, 1.1 + 0.1 * v, 3 + (v % 3) if nv > 3 else 4 + v) for v in range(nv)]
+    coeffs = rng.normal(W.coeff_count(len(vs), degree))
+    for kind in (W.KIND_EQ, W.KIND_LE):
+        # eps = 1 leaves a mix of on and off pixels on these coarse grids
+        rel = W.Relation(vs, degree, coeffs, kind, 1.0)
+        full = orc.plot_relation(rel, axes)
+        assert 0 < int(full.data.sum()) < full.data.size
+        dv = []
+        for v in vs:
+            if v not in dv:
+                dv.append(v)
+        want = full if len(dv) == len(vs) else orc.reduce(full, tuple(dv), [a[2] for a in axes])
+        check_same(eng.plot(rel, axes), want.data, f"{vs} kind {kind}")
+
+
 def test_plot_large_values_and_overflow(eng, orc):
     """Coefficients near FP32 overflow and FP64 overflow: the exact FP64 path decides."""
     axes = [(-1e3, 1e3, 300), (-1e2, 1e2, 129)]
