@@ -162,9 +162,56 @@ def pa_contract(ctx, A: BitArray, B: BitArray, keep, out: BitArray, stream=None)
     return out
 
 
+class _NetArgs:
+    """The marshalled arguments of the last pa_solve_network call, reused while
+    the same Python objects hold the same values.  Coefficients are not copied:
+    the structures point at the callers' float64 arrays, so values changed in
+    place are read by the next call as they are."""
+    __slots__ = ("axes_ref", "axes_val", "rels_ref", "rels_val", "coeffs", "exposed_val",
+                 "c_axes", "c_rels", "c_exposed")
+
+    def matches(self, axes, rels, exposed) -> bool:
+        if axes is not self.axes_ref or rels is not self.rels_ref or len(rels) != len(self.coeffs):
+            return False
+        if [tuple(a) for a in axes] != self.axes_val or tuple(exposed) != self.exposed_val:
+            return False
+        for r, (vs, deg, kind, eps), c in zip(rels, self.rels_val, self.coeffs):
+            if (r.coeffs is not c or not c.flags.c_contiguous or c.dtype != np.float64
+                    or tuple(r.vars) != vs or r.degree != deg or r.kind != kind or r.eps != eps):
+                return False
+        return True
+
+
+_last_net = None
+
+
+def _network_args(axes, rels, exposed) -> _NetArgs:
+    global _last_net
+    n = _last_net
+    if n is not None and n.matches(axes, rels, exposed):
+        return n
+    n = _NetArgs()
+    n.axes_ref, n.rels_ref = axes, rels
+    n.axes_val = [tuple(a) for a in axes]
+    n.rels_val = [(tuple(r.vars), r.degree, r.kind, r.eps) for r in rels]
+    n.exposed_val = tuple(exposed)
+    n.c_axes = _axes(axes)
+    n.c_rels, keep = _relations(rels)
+    # reuse is allowed only while each relation's coefficients are its own
+    # contiguous float64 array (no converted copy)
+    n.coeffs = [k if k is r.coeffs else None for k, r in zip(keep, rels)]
+    n.c_exposed = _i32(exposed)
+    if all(c is not None for c in n.coeffs):
+        _last_net = n
+    else:
+        n.coeffs = keep
+    return n
+
+
 def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pairs=None,
                      strict=False, stream=None, model=None) -> dict:
-    r, keep = _relations(rels)
+    na = _network_args(axes, rels, exposed)
+    r = na.c_rels
     opts = _opts(order, strict, model)
     pr = None
     if pairs is not None:
@@ -174,8 +221,8 @@ def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pa
         opts.pairs = ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32))
     st = PaStats()
     o = out.c()
-    _check(_lib().pa_solve_network(ctx, len(axes), _axes(axes), len(rels), r, len(exposed),
-                                   _i32(exposed), ctypes.byref(opts), ctypes.byref(o),
+    _check(_lib().pa_solve_network(ctx, len(axes), na.c_axes, len(rels), r, len(exposed),
+                                   na.c_exposed, ctypes.byref(opts), ctypes.byref(o),
                                    ctypes.byref(st), _stream_ptr(stream)), ctx)
     return st.as_dict()
 

@@ -144,3 +144,31 @@ def test_invalid_arguments_host(lib):
         pa.pa_valid_tolerance(bad, [(1.0, 0.0, 4), (0.0, 1.0, 4)])   # lo > hi
     with pytest.raises(pa.PaError):
         pa.pa_plan_order([(0, 1, 4)], [W.Relation((0, 3), 1, [0.0, 1.0, 1.0])], (0,))
+
+
+def test_solve_argument_reuse():
+    """The binding reuses the last call's marshalled arguments only while the
+    same objects hold the same values; coefficient arrays are pointed at, so a
+    change in place is seen without re-marshalling, and any other change (or a
+    coefficient array that needed converting) builds new arguments."""
+    s = W.chain(res=64, nrel=3)
+    a1 = pa._network_args(s.axes, s.rels, s.exposed)
+    assert pa._network_args(s.axes, s.rels, s.exposed) is a1
+    s.rels[0].coeffs[0] += 1.0
+    assert pa._network_args(s.axes, s.rels, s.exposed) is a1
+    assert a1.c_rels[0].coeffs[0] == s.rels[0].coeffs[0]
+    s.rels[1].eps = 0.5
+    a2 = pa._network_args(s.axes, s.rels, s.exposed)
+    assert a2 is not a1 and a2.c_rels[1].eps == 0.5
+    s.rels[1].vars = (2, 1)
+    a3 = pa._network_args(s.axes, s.rels, s.exposed)
+    assert a3 is not a2 and list(a3.c_rels[1].vars)[:2] == [2, 1]
+    s.axes[2] = (-1.0, 1.0, 64)
+    a4 = pa._network_args(s.axes, s.rels, s.exposed)
+    assert a4 is not a3 and a4.c_axes[2].lo == -1.0
+    a5 = pa._network_args(s.axes, s.rels, (0, 2))
+    assert a5 is not a4 and list(a5.c_exposed)[:2] == [0, 2]
+    s.rels[2].coeffs = s.rels[2].coeffs.astype(np.float32)
+    a6 = pa._network_args(s.axes, s.rels, (0, 2))
+    assert pa._network_args(s.axes, s.rels, (0, 2)) is not a6
+    assert a6.c_rels[2].coeffs[1] == float(s.rels[2].coeffs[1])
