@@ -488,6 +488,10 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
   const int nunits = nrows_w * nbat;
   const uint64_t* __restrict__ abase = d.A + (b * d.M) * d.a_row_words;
   const int64_t arw = d.a_row_words;
+  int* wcount = reinterpret_cast<int*>(bar + 1) + warp;
+  if (lane == 0) *wcount = 0;
+  int wbase = 0;
+  __syncwarp();
   auto load_unit = [&](int u) -> uint64_t {
     if (u >= nunits) return 0ull;
     const int i = (nbat == 1) ? u : u / nbat;
@@ -528,43 +532,65 @@ rowor_tile_kernel(const RowOrDesc* __restrict__ descs, const CUtensorMap* __rest
         f1 = a & ~(m16 | f4 * 0xFull);
       }
       const int c = full ? 1 : __popcll(f16) + __popcll(f4) + __popcll(f1);
-      // this lane's entries are [o, o + c) of the unit's T, in a fixed order
-      int o = c;
-#pragma unroll
-      for (int sh = 1; sh < 32; sh <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, o, sh);
-        if (lane >= sh) o += v;
-      }
-      const int T = __shfl_sync(0xffffffffu, o, 31);
-      o -= c;
+      const int T = (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
       if (d.stat && lane == 0) atomicAdd(d.stat, (unsigned long long)T * G);
-      for (int w0 = 0; w0 < T; w0 += kListWin) {
-        const int w1 = min(T, w0 + kListWin);
-        if (o < w1 && o + c > w0) {
-          // write the entries with index in [w0, w1)
-          int e = o;
-          auto put = [&](int row) {
-            if (e >= w0 && e < w1) list[e - w0] = (uint16_t)row;
-            ++e;
-          };
-          if (full) {
-            put(t6 + base / 64);
-          } else {
-            for (uint64_t m = f16; m; m &= m - 1) put(t4 + (base + __ffsll((long long)m) - 1) / 16);
-            for (uint64_t m = f4; m; m &= m - 1) put(t2 + (base + __ffsll((long long)m) - 1) / 4);
-            for (uint64_t m = f1; m; m &= m - 1) put(base + __ffsll((long long)m) - 1);
-          }
+      if (T <= kListWin) {
+        // one window: each lane claims its slots from the warp's counter,
+        // which only grows (this unit's slots start at the units' running
+        // total, known to every lane), so it never needs resetting
+        int e = c ? atomicAdd(wcount, c) - wbase : 0;
+        if (full) {
+          list[e] = (uint16_t)(t6 + base / 64);
+        } else {
+          for (uint64_t m = f16; m; m &= m - 1) list[e++] = (uint16_t)(t4 + (base + __ffsll((long long)m) - 1) / 16);
+          for (uint64_t m = f4; m; m &= m - 1) list[e++] = (uint16_t)(t2 + (base + __ffsll((long long)m) - 1) / 4);
+          for (uint64_t m = f1; m; m &= m - 1) list[e++] = (uint16_t)(base + __ffsll((long long)m) - 1);
         }
+        wbase += T;
         // pad to a whole number of rounds with the sentinel row (4P entries,
         // which is more than one per lane when the groups are narrow)
-        const int n = w1 - w0;
-        for (int t = lane; t < 4 * P; t += 32) list[n + t] = (uint16_t)sent;
+        for (int t = lane; t < 4 * P; t += 32) list[T + t] = (uint16_t)sent;
         __syncwarp();
-        for (int e = grp; e < n; e += 4 * P) {
-          const int i0 = list[e], i1 = list[e + P], i2 = list[e + 2 * P], i3 = list[e + 3 * P];
+        for (int e2 = grp; e2 < T; e2 += 4 * P) {
+          const int i0 = list[e2], i1 = list[e2 + P], i2 = list[e2 + 2 * P], i3 = list[e2 + 3 * P];
           acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
         }
         __syncwarp();
+      } else {
+        // several windows: this lane's entries are [o, o + c) of the unit's
+        // T in a fixed order, and each window writes the ones inside it
+        int o = c;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, o, sh);
+          if (lane >= sh) o += v;
+        }
+        o -= c;
+        for (int w0 = 0; w0 < T; w0 += kListWin) {
+          const int w1 = min(T, w0 + kListWin);
+          if (o < w1 && o + c > w0) {
+            int e = o;
+            auto put = [&](int row) {
+              if (e >= w0 && e < w1) list[e - w0] = (uint16_t)row;
+              ++e;
+            };
+            if (full) {
+              put(t6 + base / 64);
+            } else {
+              for (uint64_t m = f16; m; m &= m - 1) put(t4 + (base + __ffsll((long long)m) - 1) / 16);
+              for (uint64_t m = f4; m; m &= m - 1) put(t2 + (base + __ffsll((long long)m) - 1) / 4);
+              for (uint64_t m = f1; m; m &= m - 1) put(base + __ffsll((long long)m) - 1);
+            }
+          }
+          const int n = w1 - w0;
+          for (int t = lane; t < 4 * P; t += 32) list[n + t] = (uint16_t)sent;
+          __syncwarp();
+          for (int e2 = grp; e2 < n; e2 += 4 * P) {
+            const int i0 = list[e2], i1 = list[e2 + P], i2 = list[e2 + 2 * P], i3 = list[e2 + 3 * P];
+            acc |= bs[i0 * G + lig] | bs[i1 * G + lig] | bs[i2 * G + lig] | bs[i3 * G + lig];
+          }
+          __syncwarp();
+        }
       }
     }
     if (q == nbat - 1) {
