@@ -244,7 +244,13 @@ pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t
  * the order chosen by opts->order, and leave the array over `exposed` (in that
  * axis order) in `out`.  nexposed = 0 gives one bit: does the system have a
  * solution pixel.  opts and stats may be NULL.  The order is planned on the
- * host from the shapes alone, so the call never waits for the device. */
+ * host from the shapes alone, so the call never waits for the device.
+ * The context keeps the program of its last call: a call whose arguments (the
+ * coefficients included, compared by value), stream and output pointer, and
+ * the context's path, rates, join logs and profiling state, are all the same
+ * skips planning and launches that program again.  Every call still reads the
+ * host coefficients, uploads its descriptors and runs every kernel.  Orders of
+ * PA_ORDER_LEARNED are never kept (the model may change between calls). */
 pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,
                            const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
                            const pa_options* opts, pa_array* out, pa_stats* stats,

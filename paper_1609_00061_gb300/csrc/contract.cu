@@ -320,7 +320,8 @@ void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows,
 //      split each word into maximal all-ones aligned blocks of 64, 16, 4 and 1
 //      bits (a few bit operations), counting them;
 //   2. every lane writes the table rows of its blocks into the warp's list in
-//      shared memory;
+//      shared memory (256 entries: slots taken from a warp counter; a row
+//      with more blocks goes through the list in ordered windows);
 //   3. the warp splits into 32/Nt groups of Nt lanes; group g ORs table rows
 //      list[g], list[g + 32/Nt], ... (four loads in flight per lane), lane l of
 //      a group holding word n0 + l;
