@@ -786,6 +786,23 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<size_t> coeff_off(nrel);
+  // Words per block: about 2048, so that a block's set-up (row polynomials,
+  // centre table copy) is spread over many words; 1024 when that would leave
+  // fewer than three blocks per SM (a call with a few large plots), so that
+  // every SM holds several blocks.
+  int64_t tile_words = 2048;
+  {
+    int64_t blocks = 0;
+    for (const PlotReq& q : reqs) {
+      const std::vector<int> dv = distinct_vars(*q.rel);
+      int64_t nrows = 1;
+      for (size_t k = 0; k + 1 < dv.size(); ++k) nrows *= q.axes[dv[k]].res;
+      const int64_t rw = (q.axes[dv.back()].res + 63) / 64;
+      const int64_t rpt = std::max<int64_t>(1, std::min<int64_t>(256, 2048 / rw));
+      blocks += (nrows + rpt - 1) / rpt;
+    }
+    if (blocks < 3 * 152) tile_words = 1024;
+  }
   int64_t tiles = 0, max_tile_words = 1, ycen = 0;
   std::vector<CentreTab> tabs;  // one per distinct last-port axis of the hoisted jobs
   int max_rows = 1, max_deg = 0, common_deg = reqs[0].rel->degree, max_res_last = 1;
@@ -857,9 +874,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
         off += (int32_t)coeff_count(r.arity - 1, r.degree - j);
       }
     }
-    // about 2048 words per block: the block's set-up (centre table, row
-    // polynomials) is spread over enough words
-    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(256, 2048 / J.row_words));
+    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(256, tile_words / J.row_words));
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);
