@@ -341,6 +341,25 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
             "timing": "batched: CUDA events around graph replays; plain: host clock, synchronised"}
 
 
+def rank_system(W, rank):
+    """The chain instance rank `rank` solves: same shape on every rank, its own
+    coefficients (seed + rank), so per-rank work is fixed as ranks are added."""
+    return W.chain(res=2048, nrel=8, seed=W.SEED_BASE + 2 + rank)
+
+
+def whole_job(local, units_per_rank, world, dist=None, device="cpu"):
+    """The slowest rank's duration (max over ranks) and the whole-job rate:
+    every rank processed units_per_rank units, so the job processed
+    world x units_per_rank in that time.  Returns (duration, rate per unit of
+    duration)."""
+    import torch
+    t = torch.tensor([float(local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return tmax, world * units_per_rank / tmax
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1609_00061_gb300 as pa
@@ -353,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
     # path choice then weighs each cluster with those rates
     rates = eng.autotune()
     eng.set_path(args.path)
-    sysm = W.chain(res=2048, nrel=8, seed=W.SEED_BASE + 2 + rank)
+    sysm = rank_system(W, rank)
     # one logged solve measures the densities of this system's intermediates,
     # which the automatic path choice then prefers to its independence estimate
     _, _, observed, _ = eng.log_joins(sysm)
@@ -401,12 +420,9 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{dev}")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     ops = st["pixel_ops_dense"]
-    value = world * ops / (ms_max / 1e3) / 1e9
+    ms_max, ops_per_ms = whole_job(ms, ops, world, dist, f"cuda:{dev}")
+    value = ops_per_ms * 1e3 / 1e9
 
     # end to end through the public call: host coefficients in, output words out
     host_out = torch.empty(out.words.numel(), dtype=torch.int64, pin_memory=True)
@@ -421,10 +437,8 @@ def run_ours(args, rank, world, local_rank):
         host_out.copy_(out.words, non_blocking=True)
         stream.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{dev}")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * ops / float(e2e_t.item()) / 1e9
+    _, ops_per_s = whole_job(e2e_s, ops, world, dist, f"cuda:{dev}")
+    e2e_value = ops_per_s / 1e9
 
     if rank != 0:
         eng.close()
