@@ -567,7 +567,9 @@ double or_density(double rho, double n);
 
 // Tensor-core path or row-OR for a matrix-form cluster?  Forced by
 // pa_set_contract_path, else the faster by the context's measured rates: the
-// row-OR does (set bits of A) x (words per B row) word ORs, the tensor path
+// row-OR is costed as (set bits of A) x (words per B row) word ORs at the rate
+// measured on random operands (runs of set bits make it faster than that,
+// so the estimate errs towards the tensor path), the tensor path
 // every multiply-add of its padded 128 x BN x 128 tiles (its rate includes
 // the expansion of both operands).  `ra` is A's estimated density (< 0:
 // unknown).

@@ -5,8 +5,10 @@
 //   A[b][m][k]  (k packed along rows)   and   B[b][k][n]  (n packed along rows),
 // the cluster is C[b][m][n] = OR_k A[b][m][k] AND B[b][k][n], computed row-wise:
 // row (b, m) of C is the OR of the rows B[b][k][:] selected by the set bits of
-// row (b, m) of A.  Curve plots are sparse, so the work is proportional to the
-// number of set bits of A times the packed width of B, not to M*K*N.
+// row (b, m) of A.  Curve plots are sparse and their set bits come in runs, so
+// with ORs of aligned blocks of B rows the work is proportional to the number
+// of maximal aligned all-ones blocks of A (at most its set bits) times the
+// packed width of B, not to M*K*N.
 #include <cuda.h>
 #include <string.h>
 
