@@ -166,7 +166,9 @@ typedef struct pa_batch pa_batch;
 
 /* Create a context on `device`.  workspace_cap bounds the scratch memory the
  * context may hold (0: no bound).  Returns PA_ERR_CUDA when the device cannot
- * be used (no GPU, wrong architecture). */
+ * be used (no GPU, wrong architecture).  A context is used by one host thread
+ * at a time, and its calls share one workspace: calls on different streams
+ * must be ordered by the caller (one context per stream otherwise). */
 pa_status pa_create(pa_ctx** ctx, int device, size_t workspace_cap);
 void pa_destroy(pa_ctx* ctx);
 const char* pa_last_error(const pa_ctx* ctx);
