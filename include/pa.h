@@ -137,7 +137,9 @@ typedef struct {
 typedef struct {
   double pixels_plotted;     /* sum over relations of the pixels evaluated */
   double pixel_ops_dense;    /* sum over joins of r^Lambda (Sec. 3.5, naive cost) */
-  double words_or_executed;  /* 64-bit OR words the contraction kernels read */
+  double words_or_executed;  /* reserved, 0: the table words the row-OR kernels
+                                OR are counted only in profiling mode and
+                                reported by pa_profile_read ("words_or") */
   int32_t n_plots;
   int32_t n_joins;
   int32_t n_reshapes;
