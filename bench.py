@@ -279,21 +279,15 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     import torch
     from paper_1609_00061_gb300 import learned as L
 
-    def usable(nets):
-        keep = []
-        for n in nets:
-            _, ops, peak = pa.pa_plan_order(n.axes, n.rels, n.exposed)
-            if peak <= (1 << 30) and ops <= 1e13:
-                keep.append(n)
-        return keep
-
+    usable = L.usable_networks
     t0 = time.perf_counter()
     train = usable(W.random_networks(n_train, seed=W.SEED_BASE + 50))
     X, T, D = L.collect_logs(eng, train, orders_per_system=3, seed=2)
     model = pa.CostModel(eng, hidden=128, nlayers=3, seed=W.SEED_BASE + 5)
     hist = model.train(X, T, epochs=150, batch=256, lr=2e-3)
     train_s = time.perf_counter() - t0
-    nets = usable(W.random_networks(n_eval, seed=W.SEED_BASE + 5))
+    drawn = W.random_networks(n_eval, seed=W.SEED_BASE + 5)
+    nets = usable(drawn)
     stream = torch.cuda.current_stream()
 
     def time_batch(order):
@@ -327,7 +321,11 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     model.close()
     return {"workload": "random relation networks: 10-16 vars, 12-20 relations of arity 2-3, "
                         "cubics N(0,1), 128/256/512 px per axis, 2-3 exposed, seed 0x160900061+5",
-            "networks": len(nets), "train_networks": len(train), "train_samples": int(len(T)),
+            "networks": len(nets), "networks_drawn": len(drawn),
+            "networks_dropped": len(drawn) - len(nets),
+            "drop_rule": f"greedy plan's largest intermediate > 2^30 bits or sum of r^Lambda "
+                         f"> {L.MAX_PIXEL_OPS:.0e} pixel-ops",
+            "train_networks": len(train), "train_samples": int(len(T)),
             "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
             "plain_greedy_systems_per_s": len(nets) / plain_s,
             "batched_greedy_systems_per_s": len(nets) / g_s,

@@ -118,8 +118,13 @@ typedef enum {
   PA_ORDER_GREEDY = 0, /* repeatedly join the pair with the smallest result */
   PA_ORDER_GIVEN = 1,  /* join the pairs listed in pa_options.pairs */
   PA_ORDER_LEFT = 2,   /* fold the relations left to right */
-  PA_ORDER_LEARNED = 3 /* rank candidate orders with a learned cost model
-                          (pa_options.model); the greedy order is the fallback */
+  PA_ORDER_LEARNED = 3, /* rank candidate orders with a learned cost model
+                           (pa_options.model); the greedy order is the fallback */
+  PA_ORDER_OPTIMAL = 4  /* the pairwise cluster tree of least naive cost
+                           sum r^Lambda (Sec. 3.5, cost polynomial), ties to the
+                           smaller parallel cost: exact over every pairwise
+                           tree up to 14 relations, over trees of connected
+                           clusters from 15 to 20; greedy beyond */
 } pa_order;
 
 typedef struct pa_mlp pa_mlp;
@@ -281,28 +286,29 @@ pa_status pa_batch_stats(const pa_batch* batch, pa_stats* stats);
 void pa_batch_destroy(pa_batch* batch);
 
 /* pa_solve_network for callers that cannot let the library allocate memory:
- * code running while a CUDA graph is being captured (cudaMalloc and
- * cudaMallocHost are not allowed in a capture), real-time loops that cannot
- * afford the device-wide synchronisation of cudaFree, and hosts whose memory
- * is budgeted by someone else.  It allocates nothing: no cudaMalloc, no
+ * real-time loops that cannot afford the device-wide synchronisation of
+ * cudaFree, hosts whose GPU memory is budgeted by someone else (a serving
+ * process that hands the library no allocator), and code that must not grow
+ * its footprint after start-up.  It allocates nothing: no cudaMalloc, no
  * cudaFree, no pinned host memory, no context.  Its workspace is one static
  * device array of PA_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which loads
  * the library holds until the process exits; the inputs and `out` are the
  * caller's, exactly as for pa_solve_network, and the results are identical.
- * The paper has no counterpart: this is an engineering variant of Sec. 3.6.
+ * The paper has no counterpart.
  *   - Runs on the current CUDA device.  The first call on a device looks up the
- *     array's device address (cudaGetSymbolAddress) and caches it; make that
- *     first call before any stream capture.
+ *     array's device address (cudaGetSymbolAddress) and caches it.
  *   - A system whose workspace would exceed the array returns PA_ERR_TOO_LARGE
  *     before any launch; stats->workspace_bytes (when stats is not NULL) then
  *     holds the bytes it would need.
  *   - Every call shares the array and sees the previous call's contents; each
  *     call clears what must start at zero.  Calls whose work overlaps on the
  *     GPU (other streams, other threads) race on the array: order them.
+ *   - Orders: PA_ORDER_GREEDY, PA_ORDER_LEFT and PA_ORDER_GIVEN.  The learned
+ *     order needs a context's model and returns PA_ERR_INVALID_ARG here.
  *   - Argument errors return PA_ERR_INVALID_ARG; there is no context, so no
  *     message; a device wait that runs out is not reported by this entry.
- * The descriptor upload reads pageable host memory and returns once the
- * driver has copied it. */
+ *   - The descriptor upload reads pageable host memory and returns once the
+ *     driver has copied it. */
 #define PA_STATIC_SCRATCH_BYTES (16u << 20)
 pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes, int32_t nrel,
                                   const pa_relation* rels, int32_t nexposed,
@@ -358,8 +364,10 @@ pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts,
 pa_status pa_plan_learned(pa_ctx* ctx, const pa_mlp* model, int32_t nsys, const pa_system* systems,
                           int32_t ncand, int32_t* pairs_out, int32_t* learned, float* pred_us);
 
-/* The join order pa_solve_network would use (host only, no GPU): writes
- * 2*(nrel-1) slot indices into pairs_out (same numbering as pa_options.pairs). */
+/* The join order pa_solve_network would use (host only, no GPU) for order
+ * PA_ORDER_GREEDY, PA_ORDER_LEFT or PA_ORDER_OPTIMAL: writes 2*(nrel-1) slot
+ * indices into pairs_out (same numbering as pa_options.pairs), the naive cost
+ * sum r^Lambda of its joins and its largest intermediate in bits. */
 pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const pa_relation* rels,
                         int32_t nexposed, const int32_t* exposed, int32_t order,
                         int32_t* pairs_out, double* pixel_ops_out, int64_t* peak_bits_out);

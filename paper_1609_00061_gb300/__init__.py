@@ -24,7 +24,7 @@ from ._native import PaArray, PaAxis, PaOptions, PaRates, PaRelation, PaStats, P
 PA_OK = 0
 STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
           4: "PA_ERR_OOM", 5: "PA_ERR_CUDA", 6: "PA_ERR_TIMEOUT"}
-ORDERS = {"greedy": 0, "given": 1, "left": 2, "learned": 3}
+ORDERS = {"greedy": 0, "given": 1, "left": 2, "learned": 3, "optimal": 4}
 N_FEATURES = 16
 
 

@@ -1305,7 +1305,7 @@ void check_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel
   }
   n.order = opts ? opts->order : PA_ORDER_GREEDY;
   PA_CHECK_ARG(n.order == PA_ORDER_GREEDY || n.order == PA_ORDER_GIVEN || n.order == PA_ORDER_LEFT ||
-                   n.order == PA_ORDER_LEARNED,
+                   n.order == PA_ORDER_LEARNED || n.order == PA_ORDER_OPTIMAL,
                "opts: unknown order");
   PA_CHECK_ARG(n.order != PA_ORDER_LEARNED || opts->model, "opts: PA_ORDER_LEARNED needs a model");
   n.pairs = nullptr;
@@ -2415,7 +2415,8 @@ pa_status pa_plan_order(int32_t nvars, const pa_axis* axes, int32_t nrel, const 
   try {
     check_axes(ctx, nvars, axes);
     PA_CHECK_ARG(nrel >= 1 && rels && (nexposed == 0 || exposed), "null pointer");
-    PA_CHECK_ARG(order == PA_ORDER_GREEDY || order == PA_ORDER_LEFT, "order");
+    PA_CHECK_ARG(order == PA_ORDER_GREEDY || order == PA_ORDER_LEFT || order == PA_ORDER_OPTIMAL,
+                 "order");
     for (int i = 0; i < nrel; ++i) check_relation(ctx, rels[i], nvars);
     std::vector<double> vres(nvars);
     for (int v = 0; v < nvars; ++v) vres[v] = axes[v].res;
@@ -2487,6 +2488,8 @@ extern "C" pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes,
     base = g_static_addr[dev];
   }
   pa_ctx* ctx = nullptr;  // no context: errors are reported by the return code only
+  // the learned order ranks candidates with a context's model: not available here
+  if (opts && opts->order == PA_ORDER_LEARNED) return PA_ERR_INVALID_ARG;
   std::vector<Network> nets(1);
   try {
     check_network(ctx, nvars, axes, nrel, rels, nexposed, exposed, opts, out, nets[0]);

@@ -135,6 +135,129 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
   return plan_joins_policy(nvars, vres, rel_vars, exposed, order, given_pairs, 0);
 }
 
+// ----------------------------------------------------- optimal cluster tree
+// The pairwise cluster tree of least naive cost (Sec. 3.5: the cost of a tree
+// is the sum over its clusters of r^Lambda, Lambda the links of the cluster's
+// children; the parallel cost adds only the most expensive child chain).
+// Dynamic programming over subsets S of the relations: a subset's result
+// keeps K(S) = (variables of S) & (exposed variables | variables of every
+// relation outside S), which does not depend on how S was joined, so
+//   best(S) = min over splits S = S1 + S2 of best(S1) + best(S2) + r^(V(S1) | V(S2)),
+// V(single relation) = its variables, V(S) = K(S) otherwise.  Ties go to the
+// smaller parallel cost, then to the first split in enumeration order.  Up to
+// 14 relations every subset is searched, so the minimum is over all pairwise
+// trees.  From 15 to 20 relations only connected subsets are (two relations
+// are adjacent when they share a variable): the minimum is then over trees
+// whose clusters are all connected, which excludes outer products of
+// unrelated parts and keeps the subsets few.  Returns false (plan untouched)
+// beyond 20 relations or 64 variables, or for a disconnected network of more
+// than 14 relations.
+bool plan_optimal(int nvars, const std::vector<double>& vres,
+                  const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
+                  Plan& plan) {
+  const int n = (int)rel_vars.size();
+  if (n < 1 || n > kMaxOptimalRelations || nvars > 64) return false;
+  std::vector<uint64_t> rmask(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int v : rel_vars[i]) rmask[i] |= 1ull << v;
+  uint64_t emask = 0;
+  for (int v : exposed) emask |= 1ull << v;
+  std::vector<uint32_t> adj(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (i != j && (rmask[i] & rmask[j])) adj[i] |= 1u << j;
+  const uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1);
+  auto connected = [&](uint32_t S) {
+    uint32_t seen = S & (~S + 1), frontier = seen;
+    while (frontier) {
+      uint32_t nx = 0;
+      for (uint32_t f = frontier; f; f &= f - 1) nx |= adj[__builtin_ctz(f)];
+      nx &= S & ~seen;
+      seen |= nx;
+      frontier = nx;
+    }
+    return seen == S;
+  };
+  const bool only_connected = n > 14;
+  if (only_connected && !connected(full)) return false;
+  auto size_of = [&](uint64_t m) {
+    double s = 1.0;
+    for (; m; m &= m - 1) s *= vres[__builtin_ctzll(m)];
+    return s;
+  };
+  const size_t N = (size_t)1 << n;
+  std::vector<double> cost(N, INFINITY), pcost(N, INFINITY);
+  std::vector<uint64_t> vmask(N, 0);
+  std::vector<uint32_t> split(N, 0);
+  std::vector<uint64_t> inner(N, 0);
+  for (uint32_t S = 1; S <= full && S != 0; ++S) {
+    const uint32_t low = S & (~S + 1);
+    inner[S] = inner[S & (S - 1)] | rmask[__builtin_ctz(S)];
+    if (S == low) {
+      cost[S] = 0.0;
+      pcost[S] = 0.0;
+      vmask[S] = rmask[__builtin_ctz(S)];
+      continue;
+    }
+    if (only_connected && !connected(S)) continue;
+    uint64_t outside = emask;
+    for (uint32_t o = full & ~S; o; o &= o - 1) outside |= rmask[__builtin_ctz(o)];
+    vmask[S] = inner[S] & outside;
+    // S1 runs over the proper submasks of S that hold S's lowest relation
+    const uint32_t rest = S ^ low;
+    for (uint32_t sub = (rest - 1) & rest;; sub = (sub - 1) & rest) {
+      const uint32_t S1 = sub | low, S2 = S ^ S1;
+      if (S2 != 0 && cost[S1] < INFINITY && cost[S2] < INFINITY) {
+        const double node = size_of(vmask[S1] | vmask[S2]);
+        const double c = cost[S1] + cost[S2] + node;
+        const double pc = node + std::max(pcost[S1], pcost[S2]);
+        if (c < cost[S] || (c == cost[S] && pc < pcost[S])) {
+          cost[S] = c;
+          pcost[S] = pc;
+          split[S] = S1;
+        }
+      }
+      if (sub == 0) break;
+    }
+  }
+  if (!(cost[full] < INFINITY)) return false;
+  // emit the joins bottom-up; slots 0..n-1 are the relations
+  Plan out;
+  std::vector<std::vector<int>> slot_vars;
+  for (auto& rv : rel_vars) {
+    std::vector<int> d;
+    for (int v : rv)
+      if (std::find(d.begin(), d.end(), v) == d.end()) d.push_back(v);
+    slot_vars.push_back(d);
+  }
+  struct Emit {
+    static int go(uint32_t S, const std::vector<uint32_t>& split, const std::vector<uint64_t>& vmask,
+                  const std::vector<double>& vres, int n, std::vector<std::vector<int>>& slot_vars,
+                  Plan& out) {
+      if ((S & (S - 1)) == 0) return __builtin_ctz(S);
+      const uint32_t S1 = split[S], S2 = S ^ S1;
+      const int a = go(S1, split, vmask, vres, n, slot_vars, out);
+      const int b = go(S2, split, vmask, vres, n, slot_vars, out);
+      Join jn;
+      jn.a = a;
+      jn.b = b;
+      jn.keep.clear();
+      std::vector<int> u = set_union(slot_vars[a], slot_vars[b]);
+      for (int v : u)
+        if (vmask[S] >> v & 1) jn.keep.push_back(v);
+      jn.cost = set_size(u, vres);
+      out.joins.push_back(jn);
+      out.pixel_ops += jn.cost;
+      out.peak_bits = std::max(out.peak_bits, set_size(jn.keep, vres));
+      slot_vars.push_back(jn.keep);
+      return n + (int)out.joins.size() - 1;
+    }
+  };
+  out.root = Emit::go(full, split, vmask, vres, n, slot_vars, out);
+  plan = out;
+  return true;
+}
+
 // policy (order == PA_ORDER_GREEDY): 0 greedy as documented; 1 smallest cost
 // r^Lambda first; 2 + seed: at every step a seeded random pick among the three
 // best greedy pairs (candidate orders for the learned cost model).
@@ -150,6 +273,10 @@ Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
     return z ^ (z >> 31);
   };
   Plan plan;
+  if (order == PA_ORDER_OPTIMAL) {
+    if (plan_optimal(nvars, vres, rel_vars, exposed, plan)) return plan;
+    order = PA_ORDER_GREEDY;  // beyond the search's limits: the greedy order
+  }
   int nrel = (int)rel_vars.size();
   // live slots: slot id -> variable set
   std::vector<std::vector<int>> slot_vars;

@@ -32,6 +32,13 @@ Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
                        uint64_t policy);
 bool plan_valid_given(int nrel, int npairs, const int32_t* pairs);
 
+// The pairwise cluster tree of least naive cost (PA_ORDER_OPTIMAL); false
+// when the network is beyond the exact search's limits.
+constexpr int kMaxOptimalRelations = 20;
+bool plan_optimal(int nvars, const std::vector<double>& vres,
+                  const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
+                  Plan& plan);
+
 pa_status tree_cost(int32_t nlinks, const double* link_res, int32_t npacks,
                     const int32_t* pack_nports, const int32_t* pack_links, int32_t nouter,
                     const int32_t* outer_links, int32_t njoins, const int32_t* join_nchildren,

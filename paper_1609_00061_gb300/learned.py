@@ -12,6 +12,23 @@ import math
 
 import numpy as np
 
+# Networks the batch benchmark and the tests solve: the greedy order's largest
+# intermediate at most 2^30 bits and its naive cost (sum of r^Lambda) at most
+# 1e13 pixel-ops.
+MAX_PEAK_BITS = 1 << 30
+MAX_PIXEL_OPS = 1e13
+
+
+def usable_networks(nets, max_peak_bits=MAX_PEAK_BITS, max_pixel_ops=MAX_PIXEL_OPS):
+    """The networks whose greedy plan stays within the limits above (host only)."""
+    from . import pa_plan_order
+    keep = []
+    for n in nets:
+        _, ops, peak = pa_plan_order(n.axes, n.rels, n.exposed)
+        if peak <= max_peak_bits and ops <= max_pixel_ops:
+            keep.append(n)
+    return keep
+
 
 def join_sequence_shapes(system, pairs):
     """Per join of a pair sequence: (kept variables, r^Lambda, result bits).

@@ -1,8 +1,8 @@
 """pa_solve_network_static: the solve for callers that cannot let the library
-allocate memory (code inside a CUDA graph capture, real-time loops that cannot
-take cudaFree's device-wide synchronisation, hosts with their own memory
-budget).  Its workspace is a fixed device array; its results must equal those
-of pa_solve_network bit for bit, call after call, since every call reuses the
+allocate memory (real-time loops that cannot take cudaFree's device-wide
+synchronisation, serving processes whose GPU memory is budgeted by someone
+else).  Its workspace is a fixed device array; its results must equal those of
+pa_solve_network bit for bit, call after call, since every call reuses the
 same array."""
 import numpy as np
 import pytest
@@ -65,3 +65,12 @@ def test_static_rejects_oversized_system(eng):
     with pytest.raises(pa.PaError) as e:
         pa.pa_solve_network_static(sysm.axes, sysm.rels, sysm.exposed, out)
     assert e.value.status == 3
+
+
+def test_static_rejects_learned_order(eng):
+    """The learned order needs a context's cost model: refused, not replaced."""
+    sysm = W.chain(res=64, nrel=3, seed=4)
+    out = pa.BitArray.empty(sysm.exposed, [sysm.axes[v][2] for v in sysm.exposed])
+    with pytest.raises(pa.PaError) as e:
+        pa.pa_solve_network_static(sysm.axes, sysm.rels, sysm.exposed, out, order="learned")
+    assert e.value.status == 1
