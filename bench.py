@@ -230,12 +230,15 @@ def run_batched(eng, pa, W, dev, reps=5):
     pa_solve_network call per system (greedy order both ways)."""
     import torch
     systems = W.batched_chains(nsys=4096, seed=W.SEED_BASE + 4)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     b = eng.batch(systems)
     plan_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    for _ in range(2):
-        b.run()
+    b.run()
+    torch.cuda.synchronize()
+    fresh_s = time.perf_counter() - t0
+    b.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -265,7 +268,10 @@ def run_batched(eng, pa, W, dev, reps=5):
             "tensor_core_joins": int(st["n_mma"]),
             "pixel_ops_dense": st["pixel_ops_dense"],
             "batched_gpixel_ops_per_s": st["pixel_ops_dense"] / graph_s / 1e9,
-            "plan_and_capture_s": plan_s, "workspace_bytes": st["workspace_bytes"],
+            "plan_and_capture_s": plan_s,
+            "fresh_batch_systems_per_s": len(systems) / fresh_s,
+            "fresh_batch_s": fresh_s,
+            "workspace_bytes": st["workspace_bytes"],
             "timing": "batched: CUDA events around graph replays (blob copy included); "
                       "plain: host clock around the per-system calls, synchronised"}
 
@@ -275,7 +281,11 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     128/256/512 px per axis, 2-3 exposed): the cost model is trained on solver
     logs of disjoint training networks, then the evaluation networks are solved
     (a) one pa_solve_network call each, greedy order; (b) as one graph-captured
-    batch, greedy order; (c) as one graph-captured batch, learned order."""
+    batch, greedy order; (c) as one graph-captured batch, least-naive-cost
+    order (PA_ORDER_OPTIMAL); (d) as one graph-captured batch, learned order.
+    Before (d) the solver logs the greedy order of every evaluation network
+    (pa_join_log), so the judge compares a candidate's predicted time with
+    greedy's measured one."""
     import torch
     from paper_1609_00061_gb300 import learned as L
 
@@ -289,11 +299,19 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     drawn = W.random_networks(n_eval, seed=W.SEED_BASE + 5)
     nets = usable(drawn)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    for n in nets:
+        eng.log_joins(n)          # greedy's measured join times, for the judge
+    torch.cuda.synchronize()
+    judge_log_s = time.perf_counter() - t0
 
     def time_batch(order):
+        t0 = time.perf_counter()
         b = eng.batch(nets, order=order, model=model if order == "learned" else None)
-        for _ in range(2):
-            b.run()
+        b.run()
+        torch.cuda.synchronize()
+        fresh = time.perf_counter() - t0
+        b.run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -302,10 +320,12 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
         e1.record(stream)
         torch.cuda.synchronize()
         st = b.stats()
+        st["fresh_s"] = fresh
         b.close()
         return e0.elapsed_time(e1) / 1e3 / reps, st
 
     g_s, g_st = time_batch("greedy")
+    o_s, o_st = time_batch("optimal")
     l_s, l_st = time_batch("learned")
     _, learned_flags, pred = eng.plan_learned(model, nets)
     outs = [pa.BitArray.empty(n.exposed, [n.axes[v][2] for v in n.exposed], eng.device)
@@ -329,14 +349,25 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
             "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
             "plain_greedy_systems_per_s": len(nets) / plain_s,
             "batched_greedy_systems_per_s": len(nets) / g_s,
+            "batched_optimal_systems_per_s": len(nets) / o_s,
             "batched_learned_systems_per_s": len(nets) / l_s,
             "learned_vs_plain": plain_s / l_s, "learned_vs_batched_greedy": g_s / l_s,
+            "optimal_vs_batched_greedy": g_s / o_s,
             "learned_orders_kept": int(sum(learned_flags)),
+            "judge_log_s": judge_log_s,
+            "fresh_batch_s": {"greedy": g_st["fresh_s"], "optimal": o_st["fresh_s"],
+                              "learned": l_st["fresh_s"]},
             "tensor_core_joins_greedy": int(g_st["n_mma"]),
+            "tensor_core_joins_optimal": int(o_st["n_mma"]),
             "tensor_core_joins_learned": int(l_st["n_mma"]),
             "pixel_ops_dense_greedy": g_st["pixel_ops_dense"],
+            "pixel_ops_dense_optimal": o_st["pixel_ops_dense"],
             "pixel_ops_dense_learned": l_st["pixel_ops_dense"],
-            "timing": "batched: CUDA events around graph replays; plain: host clock, synchronised"}
+            "graph_launches": {"greedy": g_st["n_launches"], "optimal": o_st["n_launches"],
+                               "learned": l_st["n_launches"]},
+            "timing": "batched: CUDA events around graph replays; plain: host clock, "
+                      "synchronised; fresh: host clock around planning, capture and the "
+                      "first replay"}
 
 
 def rank_system(W, rank):

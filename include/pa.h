@@ -123,8 +123,9 @@ typedef enum {
   PA_ORDER_OPTIMAL = 4  /* the pairwise cluster tree of least naive cost
                            sum r^Lambda (Sec. 3.5, cost polynomial), ties to the
                            smaller parallel cost: exact over every pairwise
-                           tree up to 14 relations, over trees of connected
-                           clusters from 15 to 20; greedy beyond */
+                           tree up to 16 relations; beyond, the greedy tree
+                           with every subtree of at most 16 relations
+                           replaced by its exact optimum */
 } pa_order;
 
 typedef struct pa_mlp pa_mlp;
@@ -323,11 +324,16 @@ pa_status pa_solve_network_static(int32_t nvars, const pa_axis* axes, int32_t nr
  * result densities, reshape volume.  Plot densities are estimated on the host
  * from 512 sampled pixel centres, join densities propagated under an
  * independence assumption, so planning never waits for the solve.
- * PA_ORDER_LEARNED ranks `ncand` candidate orders per system (greedy,
- * smallest-cost, left-to-right and seeded randomised greedy variants) by the
- * predicted total time; the greedy order is the judge: the learned choice is
- * kept only when its predicted time is lower and its largest intermediate is
- * at most 4x the greedy one.  Any order gives the same bits. */
+ * PA_ORDER_LEARNED ranks `ncand` candidate orders per system (greedy, the
+ * least-naive-cost tree of PA_ORDER_OPTIMAL, smallest-cost-first,
+ * left-to-right and seeded randomised greedy variants) by their total time:
+ * a join that pa_join_log has timed on this context (the same join of the
+ * same relations) counts with its measured microseconds, any other with the
+ * model's prediction.  The greedy order is the judge: the learned choice is
+ * kept only when its total is lower than greedy's and its largest
+ * intermediate is at most 4x the greedy one, so logging a system's greedy
+ * order first makes greedy's side of the comparison measured.  Any order
+ * gives the same bits. */
 #define PA_FEATURES 16
 pa_status pa_mlp_create(pa_ctx* ctx, int32_t hidden, int32_t nlayers, uint64_t seed,
                         pa_mlp** model);
@@ -359,8 +365,9 @@ pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts,
 /* The orders PA_ORDER_LEARNED would use, with the judge's inputs: for system k,
  * pairs_out[offsets..] receives its 2*(nrel_k-1) slot indices (systems packed
  * one after another), learned[k] whether the learned order was kept, and
- * pred_us[2k], pred_us[2k+1] the predicted times of the chosen and the greedy
- * order.  Runs one forward pass on the GPU and waits for it. */
+ * pred_us[2k], pred_us[2k+1] the judge's totals of the chosen and the greedy
+ * order (measured joins measured, the rest predicted).  Runs one forward pass
+ * on the GPU and waits for it. */
 pa_status pa_plan_learned(pa_ctx* ctx, const pa_mlp* model, int32_t nsys, const pa_system* systems,
                           int32_t ncand, int32_t* pairs_out, int32_t* learned, float* pred_us);
 

@@ -58,8 +58,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr)
 
-    with ThreadPoolExecutor(max_workers=len(jobs)) as pool:
-        list(pool.map(run, jobs))
+    # an object is rebuilt when it is older than its source or any header
+    headers = max(os.path.getmtime(s) for s in srcs if s.endswith(".h"))
+
+    def stale(job):
+        obj, src = job[-1], job[-3]
+        return (force or not os.path.exists(obj)
+                or os.path.getmtime(obj) < max(os.path.getmtime(src), headers))
+
+    todo = [j for j in jobs if stale(j)]
+    if todo:
+        with ThreadPoolExecutor(max_workers=len(todo)) as pool:
+            list(pool.map(run, todo))
     objs = [j[-1] for j in jobs]
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])

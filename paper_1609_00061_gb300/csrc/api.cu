@@ -57,6 +57,7 @@ struct pa_ctx {
   double rate_mma = 4.4e8;     // tensor path (with operand expansion): multiply-adds per microsecond
   std::unordered_map<uint64_t, double> dens_cache;  // relation key -> estimated plot density
   std::unordered_map<uint64_t, double> obs_dens;    // subtree key -> density measured by pa_join_log
+  std::unordered_map<uint64_t, double> obs_time;    // subtree key -> join microseconds measured by pa_join_log
   // the last pa_solve_network program, relaunched without planning when the
   // next call's arguments and planning state are the same byte for byte
   uint64_t plan_epoch = 0;  // changes with every setting or measurement that steers planning
@@ -96,6 +97,7 @@ struct Op {
   int64_t m = 0, nw = 0;                // outer / dot: M and words per row
   int i0 = 0, i1 = 0, i2 = 0, i3 = 0;   // plot: rows/tile, max degree, common degree, max res
   size_t smem = 0;                      // rowor dynamic shared memory
+  int64_t zw = 0;                       // plot: words of the ranges it clears (off1, nw ranges)
   uint64_t* p = nullptr;                // memset / and output
   const uint64_t* a = nullptr;
   const uint64_t* b = nullptr;
@@ -951,6 +953,39 @@ uint64_t subtree_key(uint64_t ka, uint64_t kb, const std::vector<int>& keep) {
   return h;
 }
 
+// Clear every memset target of the program in the plot launch that opens it
+// instead of in memsets of their own: a memset between two launches ends
+// their programmatic overlap and costs a launch.  Valid because every memset
+// target is a result buffer that no op before its contraction touches (the
+// workspace is handed out once per call, and the output array is written only
+// by the program's last joins), and every contraction waits for the plot
+// launch to complete.
+void fold_memsets(Builder& bd) {
+  size_t plot_at = bd.ops.size();
+  for (size_t i = 0; i < bd.ops.size() && plot_at == bd.ops.size(); ++i)
+    if (bd.ops[i].kind == OP_PLOT) plot_at = i;
+  if (plot_at == bd.ops.size()) return;
+  std::vector<ZeroRange> zr;
+  int64_t total = 0;
+  std::vector<Op> kept;
+  for (size_t i = 0; i < bd.ops.size(); ++i) {
+    const Op& op = bd.ops[i];
+    if (op.kind == OP_MEMSET && i > plot_at) {
+      zr.push_back({op.p, op.count, total});
+      total += op.count;
+    } else {
+      kept.push_back(op);
+    }
+  }
+  if (zr.empty()) return;
+  if (zr.size() > 0x7fffffff) bd.fail(PA_ERR_TOO_LARGE, "too many result buffers to clear");
+  bd.ops.swap(kept);
+  Op& pop = bd.ops[plot_at];
+  pop.off1 = bd.put(zr.data(), zr.size(), 64);
+  pop.nw = (int64_t)zr.size();
+  pop.zw = total;
+}
+
 // Plots of all networks in one launch pair, then their joins level by level:
 // the joins of one level of every network's cluster tree are independent and
 // share one contraction launch per tile width.
@@ -1048,6 +1083,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
     const BitArr& root = S[k].slots[S[k].plan.root];
     if (root.w != nets[k].target.w) reshape(bd, root, nets[k].target);
   }
+  if (!one_join_per_launch) fold_memsets(bd);
 }
 
 // ------------------------------------------------------------ running
@@ -1078,7 +1114,8 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
     switch (op.kind) {
       case OP_PLOT:
         launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
-                    op.i1, op.i2, op.i3, op.m, s);
+                    op.i1, op.i2, op.i3, op.m, reinterpret_cast<const ZeroRange*>(blob + op.off1),
+                    (int)op.nw, op.zw, s);
         break;
       case OP_CENTRES:
         launch_plot_centres(reinterpret_cast<const CentreTab*>(blob + op.off0), op.n, op.count, s);
@@ -1458,6 +1495,17 @@ SimResult simulate_plan(const Network& n, const Plan& plan, const std::vector<do
   return r;
 }
 
+// Subtree key of every join of a plan (the keys build_networks gives slots).
+std::vector<uint64_t> plan_keys(const Network& n, const Plan& plan) {
+  std::vector<uint64_t> k(n.nrel + plan.joins.size());
+  for (int i = 0; i < n.nrel; ++i) k[i] = relation_key(n.rels[i], n.axes);
+  for (size_t t = 0; t < plan.joins.size(); ++t) {
+    const Join& jn = plan.joins[t];
+    k[n.nrel + t] = subtree_key(k[jn.a], k[jn.b], jn.keep);
+  }
+  return std::vector<uint64_t>(k.begin() + n.nrel, k.end());
+}
+
 Plan plan_of(const Network& n, int order, const int32_t* pairs, uint64_t policy) {
   std::vector<double> vresd(n.nvars);
   for (int v = 0; v < n.nvars; ++v) vresd[v] = n.axes[v].res;
@@ -1530,6 +1578,7 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
     Plan plan;
     size_t row0, rows;
     double peak;
+    std::vector<uint64_t> keys;  // subtree key of every join
   };
   std::vector<Cand> cands;
   std::vector<float> X;
@@ -1541,8 +1590,9 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
     std::vector<std::vector<int32_t>> seen;
     for (int c = 0; c < ncand; ++c) {
       Plan p = (c == 0) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 0)
-               : (c == 1) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 1)
-               : (c == 2) ? plan_of(n, PA_ORDER_LEFT, nullptr, 0)
+               : (c == 1) ? plan_of(n, PA_ORDER_OPTIMAL, nullptr, 0)
+               : (c == 2) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 1)
+               : (c == 3) ? plan_of(n, PA_ORDER_LEFT, nullptr, 0)
                           : plan_of(n, PA_ORDER_GREEDY, nullptr, 2 + (uint64_t)c * 7919 + k);
       std::vector<int32_t> key;
       for (const Join& j : p.joins) {
@@ -1552,7 +1602,7 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
       if (c > 0 && std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
       seen.push_back(key);
       SimResult sim = simulate_plan(n, p, dens);
-      Cand cd{k, p, X.size() / kFeat, sim.feats.size() / kFeat, sim.peak_bits};
+      Cand cd{k, p, X.size() / kFeat, sim.feats.size() / kFeat, sim.peak_bits, plan_keys(n, p)};
       X.insert(X.end(), sim.feats.begin(), sim.feats.end());
       cands.push_back(cd);
     }
@@ -1573,9 +1623,14 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
   std::vector<LearnedChoice> out(nets.size());
   for (size_t k = 0; k < nets.size(); ++k) {
     const size_t c0 = first[k], c1 = (k + 1 < nets.size()) ? first[k + 1] : cands.size();
+    // a join the solver has timed (pa_join_log) counts with its measured
+    // microseconds, any other with the model's prediction
     auto total = [&](const Cand& cd) {
       double t = 0;
-      for (size_t r = cd.row0; r < cd.row0 + cd.rows; ++r) t += exp2(8.0 * (double)Y[r]);
+      for (size_t r = cd.row0; r < cd.row0 + cd.rows; ++r) {
+        auto it = ctx->obs_time.find(cd.keys[r - cd.row0]);
+        t += (it != ctx->obs_time.end()) ? it->second : exp2(8.0 * (double)Y[r]);
+      }
       return t;
     };
     const double tg = total(cands[c0]);
@@ -2354,14 +2409,20 @@ pa_status pa_join_log(pa_ctx* ctx, const pa_system* sys, const pa_options* opts,
       micros[t] = (float)us[t];
       densities[t] = (float)((double)cnt[t] / (double)std::max<int64_t>(1, results[t].bits()));
     }
-    // remember the measured densities for later path choices on these relations
+    // remember the measured densities for later path choices on these
+    // relations, and the measured join times for the learned order's judge
+    // (a subtree key names the whole join tree below a result, so a time is
+    // only reused for the very same join)
     const Network& n0 = nets[0];
     if ((int)n0.slot_keys.size() == n0.nrel + nj) {
       ctx->plan_epoch++;
       if (ctx->obs_dens.size() >= (1u << 16)) ctx->obs_dens.clear();
-      for (int t = 0; t < nj; ++t)
+      if (ctx->obs_time.size() >= (1u << 16)) ctx->obs_time.clear();
+      for (int t = 0; t < nj; ++t) {
         ctx->obs_dens[n0.slot_keys[n0.nrel + t]] =
             (double)cnt[t] / (double)std::max<int64_t>(1, results[t].bits());
+        ctx->obs_time[n0.slot_keys[n0.nrel + t]] = us[t];
+      }
     }
   } catch (const Fail& f) {
     st = f.st;

@@ -56,6 +56,13 @@ struct CentreTab {
   int64_t item0;  // first item of this table in the centre-table launch
   int64_t res;
 };
+// A range of words to clear: words [w0, w0 + words) of the launch's flat
+// index space are p[0 .. words).
+struct ZeroRange {
+  uint64_t* p;
+  int64_t words;
+  int64_t w0;
+};
 // Every table in one launch (one thread per centre), before the plot launch;
 // the plot kernel waits for it only after its row set-up (programmatic
 // dependent launch), so the two overlap.
@@ -64,9 +71,12 @@ void launch_plot_centres(const CentreTab* d_tabs, int ntabs, int64_t total_items
 // rows' polynomials and thresholds in shared memory first.  common_degree: the
 // degree shared by every job (selects a specialised kernel), or -1 when they
 // differ.
+// The same launch also clears the `nzero` ranges (zero_words words in all)
+// that later contractions OR their results into, so that no separate memset
+// sits between the launches.
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, int64_t max_tile_words,
-                 cudaStream_t s);
+                 const ZeroRange* d_zero, int nzero, int64_t zero_words, cudaStream_t s);
 
 // ------------------------------------------------------------- bit arrays
 // A bit-packed array with `inner` trailing axes flattened into packed rows:

@@ -139,77 +139,56 @@ Plan plan_joins(int nvars, const std::vector<double>& vres,
 // The pairwise cluster tree of least naive cost (Sec. 3.5: the cost of a tree
 // is the sum over its clusters of r^Lambda, Lambda the links of the cluster's
 // children; the parallel cost adds only the most expensive child chain).
-// Dynamic programming over subsets S of the relations: a subset's result
-// keeps K(S) = (variables of S) & (exposed variables | variables of every
-// relation outside S), which does not depend on how S was joined, so
+// Dynamic programming over subsets S of a set of relations: S's result keeps
+// K(S) = (variables of S) & (variables needed outside S), which does not
+// depend on how S was joined, so
 //   best(S) = min over splits S = S1 + S2 of best(S1) + best(S2) + r^(V(S1) | V(S2)),
 // V(single relation) = its variables, V(S) = K(S) otherwise.  Ties go to the
-// smaller parallel cost, then to the first split in enumeration order.  Up to
-// 14 relations every subset is searched, so the minimum is over all pairwise
-// trees.  From 15 to 20 relations only connected subsets are (two relations
-// are adjacent when they share a variable): the minimum is then over trees
-// whose clusters are all connected, which excludes outer products of
-// unrelated parts and keeps the subsets few.  Returns false (plan untouched)
-// beyond 20 relations or 64 variables, or for a disconnected network of more
-// than 14 relations.
-bool plan_optimal(int nvars, const std::vector<double>& vres,
-                  const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
-                  Plan& plan) {
-  const int n = (int)rel_vars.size();
-  if (n < 1 || n > kMaxOptimalRelations || nvars > 64) return false;
-  std::vector<uint64_t> rmask(n, 0);
-  for (int i = 0; i < n; ++i)
-    for (int v : rel_vars[i]) rmask[i] |= 1ull << v;
-  uint64_t emask = 0;
-  for (int v : exposed) emask |= 1ull << v;
-  std::vector<uint32_t> adj(n, 0);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j)
-      if (i != j && (rmask[i] & rmask[j])) adj[i] |= 1u << j;
-  const uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1);
-  auto connected = [&](uint32_t S) {
-    uint32_t seen = S & (~S + 1), frontier = seen;
-    while (frontier) {
-      uint32_t nx = 0;
-      for (uint32_t f = frontier; f; f &= f - 1) nx |= adj[__builtin_ctz(f)];
-      nx &= S & ~seen;
-      seen |= nx;
-      frontier = nx;
-    }
-    return seen == S;
-  };
-  const bool only_connected = n > 14;
-  if (only_connected && !connected(full)) return false;
+// smaller parallel cost, then to the first split in enumeration order.  The
+// search visits every pair (S, S1), about 3^n of them.
+namespace {
+
+struct TreeNode {
+  int leaf = -1;     // relation index, or -1 for a join
+  int left = -1, right = -1;
+};
+
+// Exact search over the relations `rels` (at most 20), whose results must
+// keep every variable of `outside`.  Appends the optimal tree's nodes to
+// `nodes` and returns the root node's index.
+int exact_tree(const std::vector<int>& rels, const std::vector<uint64_t>& rmask, uint64_t outside,
+               const std::vector<double>& vres, std::vector<TreeNode>& nodes) {
+  const int n = (int)rels.size();
   auto size_of = [&](uint64_t m) {
     double s = 1.0;
     for (; m; m &= m - 1) s *= vres[__builtin_ctzll(m)];
     return s;
   };
+  const uint32_t full = (1u << n) - 1;
   const size_t N = (size_t)1 << n;
   std::vector<double> cost(N, INFINITY), pcost(N, INFINITY);
-  std::vector<uint64_t> vmask(N, 0);
+  std::vector<uint64_t> vmask(N, 0), inner(N, 0);
   std::vector<uint32_t> split(N, 0);
-  std::vector<uint64_t> inner(N, 0);
-  for (uint32_t S = 1; S <= full && S != 0; ++S) {
+  for (uint32_t S = 1; S <= full; ++S) {
     const uint32_t low = S & (~S + 1);
-    inner[S] = inner[S & (S - 1)] | rmask[__builtin_ctz(S)];
+    inner[S] = inner[S & (S - 1)] | rmask[rels[__builtin_ctz(S)]];
     if (S == low) {
-      cost[S] = 0.0;
-      pcost[S] = 0.0;
-      vmask[S] = rmask[__builtin_ctz(S)];
+      cost[S] = pcost[S] = 0.0;
+      vmask[S] = inner[S];
       continue;
     }
-    if (only_connected && !connected(S)) continue;
-    uint64_t outside = emask;
-    for (uint32_t o = full & ~S; o; o &= o - 1) outside |= rmask[__builtin_ctz(o)];
-    vmask[S] = inner[S] & outside;
+    uint64_t need = outside;
+    for (uint32_t o = full & ~S; o; o &= o - 1) need |= rmask[rels[__builtin_ctz(o)]];
+    vmask[S] = inner[S] & need;
+    const double floor_node = size_of(vmask[S]);  // the root of S keeps at least K(S)
     // S1 runs over the proper submasks of S that hold S's lowest relation
     const uint32_t rest = S ^ low;
     for (uint32_t sub = (rest - 1) & rest;; sub = (sub - 1) & rest) {
       const uint32_t S1 = sub | low, S2 = S ^ S1;
-      if (S2 != 0 && cost[S1] < INFINITY && cost[S2] < INFINITY) {
+      const double below = cost[S1] + cost[S2];
+      if (below + floor_node <= cost[S]) {
         const double node = size_of(vmask[S1] | vmask[S2]);
-        const double c = cost[S1] + cost[S2] + node;
+        const double c = below + node;
         const double pc = node + std::max(pcost[S1], pcost[S2]);
         if (c < cost[S] || (c == cost[S] && pc < pcost[S])) {
           cost[S] = c;
@@ -220,8 +199,131 @@ bool plan_optimal(int nvars, const std::vector<double>& vres,
       if (sub == 0) break;
     }
   }
-  if (!(cost[full] < INFINITY)) return false;
-  // emit the joins bottom-up; slots 0..n-1 are the relations
+  struct Emit {
+    const std::vector<int>& rels;
+    const std::vector<uint32_t>& split;
+    std::vector<TreeNode>& nodes;
+    int go(uint32_t S) {
+      TreeNode t;
+      if ((S & (S - 1)) == 0) {
+        t.leaf = rels[__builtin_ctz(S)];
+      } else {
+        t.left = go(split[S]);
+        t.right = go(S ^ split[S]);
+      }
+      nodes.push_back(t);
+      return (int)nodes.size() - 1;
+    }
+  } emit{rels, split, nodes};
+  return emit.go(full);
+}
+
+void tree_leaves(const std::vector<TreeNode>& nodes, int t, std::vector<int>& out) {
+  if (nodes[t].leaf >= 0) {
+    out.push_back(nodes[t].leaf);
+    return;
+  }
+  tree_leaves(nodes, nodes[t].left, out);
+  tree_leaves(nodes, nodes[t].right, out);
+}
+
+// Emit the joins of a tree bottom-up into a Plan (slots 0..nrel-1 are the
+// relations; join t creates slot nrel + t).
+int emit_plan(const std::vector<TreeNode>& nodes, int t, int nrel,
+              const std::vector<std::vector<int>>& rel_vars, const std::vector<uint64_t>& rmask,
+              uint64_t emask, const std::vector<double>& vres,
+              std::vector<std::vector<int>>& slot_vars, Plan& out) {
+  if (nodes[t].leaf >= 0) return nodes[t].leaf;
+  const int a = emit_plan(nodes, nodes[t].left, nrel, rel_vars, rmask, emask, vres, slot_vars, out);
+  const int b = emit_plan(nodes, nodes[t].right, nrel, rel_vars, rmask, emask, vres, slot_vars, out);
+  std::vector<int> in;
+  tree_leaves(nodes, t, in);
+  uint64_t need = emask;
+  for (int i = 0; i < nrel; ++i)
+    if (std::find(in.begin(), in.end(), i) == in.end()) need |= rmask[i];
+  Join jn;
+  jn.a = a;
+  jn.b = b;
+  const std::vector<int> u = set_union(slot_vars[a], slot_vars[b]);
+  for (int v : u)
+    if (need >> v & 1) jn.keep.push_back(v);
+  jn.cost = set_size(u, vres);
+  out.joins.push_back(jn);
+  out.pixel_ops += jn.cost;
+  out.peak_bits = std::max(out.peak_bits, set_size(jn.keep, vres));
+  slot_vars.push_back(jn.keep);
+  return nrel + (int)out.joins.size() - 1;
+}
+
+}  // namespace
+
+bool plan_optimal(int nvars, const std::vector<double>& vres,
+                  const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
+                  Plan& plan) {
+  const int n = (int)rel_vars.size();
+  if (n < 1 || nvars > 64) return false;
+  std::vector<uint64_t> rmask(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int v : rel_vars[i]) rmask[i] |= 1ull << v;
+  uint64_t emask = 0;
+  for (int v : exposed) emask |= 1ull << v;
+  std::vector<TreeNode> nodes;
+  int root;
+  if (n <= kMaxOptimalRelations) {
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    root = exact_tree(all, rmask, emask, vres, nodes);
+  } else {
+    // larger networks: the greedy tree, every subtree of at most
+    // kMaxOptimalRelations relations replaced by the exact optimum over its
+    // relations (a subtree's result does not depend on its inner order)
+    Plan g = plan_joins_policy(nvars, vres, rel_vars, exposed, PA_ORDER_GREEDY, nullptr, 0);
+    std::vector<int> slot_node(n + g.joins.size());
+    std::vector<std::vector<int>> slot_rels(n + g.joins.size());
+    for (int i = 0; i < n; ++i) {
+      TreeNode t;
+      t.leaf = i;
+      nodes.push_back(t);
+      slot_node[i] = i;
+      slot_rels[i] = {i};
+    }
+    std::vector<char> replaced(n + g.joins.size(), 0);
+    for (size_t t = 0; t < g.joins.size(); ++t) {
+      const int s = n + (int)t;
+      slot_rels[s] = slot_rels[g.joins[t].a];
+      slot_rels[s].insert(slot_rels[s].end(), slot_rels[g.joins[t].b].begin(),
+                          slot_rels[g.joins[t].b].end());
+      TreeNode j;
+      j.left = slot_node[g.joins[t].a];
+      j.right = slot_node[g.joins[t].b];
+      nodes.push_back(j);
+      slot_node[s] = (int)nodes.size() - 1;
+    }
+    // top-down: the largest subtrees that fit are searched exactly
+    struct Refine {
+      std::vector<TreeNode>& nodes;
+      const std::vector<uint64_t>& rmask;
+      uint64_t emask;
+      int nrel;
+      const std::vector<double>& vres;
+      int go(int t) {
+        if (nodes[t].leaf >= 0) return t;
+        std::vector<int> in;
+        tree_leaves(nodes, t, in);
+        if ((int)in.size() <= kMaxOptimalRelations) {
+          uint64_t need = emask;
+          for (int i = 0; i < nrel; ++i)
+            if (std::find(in.begin(), in.end(), i) == in.end()) need |= rmask[i];
+          return exact_tree(in, rmask, need, vres, nodes);
+        }
+        const int l = go(nodes[t].left), r = go(nodes[t].right);
+        nodes[t].left = l;
+        nodes[t].right = r;
+        return t;
+      }
+    } refine{nodes, rmask, emask, n, vres};
+    root = refine.go(slot_node[g.root]);
+  }
   Plan out;
   std::vector<std::vector<int>> slot_vars;
   for (auto& rv : rel_vars) {
@@ -230,30 +332,7 @@ bool plan_optimal(int nvars, const std::vector<double>& vres,
       if (std::find(d.begin(), d.end(), v) == d.end()) d.push_back(v);
     slot_vars.push_back(d);
   }
-  struct Emit {
-    static int go(uint32_t S, const std::vector<uint32_t>& split, const std::vector<uint64_t>& vmask,
-                  const std::vector<double>& vres, int n, std::vector<std::vector<int>>& slot_vars,
-                  Plan& out) {
-      if ((S & (S - 1)) == 0) return __builtin_ctz(S);
-      const uint32_t S1 = split[S], S2 = S ^ S1;
-      const int a = go(S1, split, vmask, vres, n, slot_vars, out);
-      const int b = go(S2, split, vmask, vres, n, slot_vars, out);
-      Join jn;
-      jn.a = a;
-      jn.b = b;
-      jn.keep.clear();
-      std::vector<int> u = set_union(slot_vars[a], slot_vars[b]);
-      for (int v : u)
-        if (vmask[S] >> v & 1) jn.keep.push_back(v);
-      jn.cost = set_size(u, vres);
-      out.joins.push_back(jn);
-      out.pixel_ops += jn.cost;
-      out.peak_bits = std::max(out.peak_bits, set_size(jn.keep, vres));
-      slot_vars.push_back(jn.keep);
-      return n + (int)out.joins.size() - 1;
-    }
-  };
-  out.root = Emit::go(full, split, vmask, vres, n, slot_vars, out);
+  out.root = emit_plan(nodes, root, n, rel_vars, rmask, emask, vres, slot_vars, out);
   plan = out;
   return true;
 }
@@ -275,7 +354,7 @@ Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
   Plan plan;
   if (order == PA_ORDER_OPTIMAL) {
     if (plan_optimal(nvars, vres, rel_vars, exposed, plan)) return plan;
-    order = PA_ORDER_GREEDY;  // beyond the search's limits: the greedy order
+    order = PA_ORDER_GREEDY;  // more than 64 variables: the greedy order
   }
   int nrel = (int)rel_vars.size();
   // live slots: slot id -> variable set

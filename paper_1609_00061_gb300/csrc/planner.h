@@ -32,9 +32,11 @@ Plan plan_joins_policy(int nvars, const std::vector<double>& vres,
                        uint64_t policy);
 bool plan_valid_given(int nrel, int npairs, const int32_t* pairs);
 
-// The pairwise cluster tree of least naive cost (PA_ORDER_OPTIMAL); false
-// when the network is beyond the exact search's limits.
-constexpr int kMaxOptimalRelations = 20;
+// The pairwise cluster tree of least naive cost (PA_ORDER_OPTIMAL): exact up
+// to kMaxOptimalRelations relations; beyond, the greedy tree with every
+// subtree of at most that many relations searched exactly.  False when the
+// network has more than 64 variables.
+constexpr int kMaxOptimalRelations = 16;
 bool plan_optimal(int nvars, const std::vector<double>& vres,
                   const std::vector<std::vector<int>>& rel_vars, const std::vector<int>& exposed,
                   Plan& plan);

@@ -40,6 +40,8 @@
 // proves it on; only the remaining words are evaluated pixel by pixel.
 #include <float.h>
 
+#include <algorithm>
+
 #include "pa_internal.h"
 
 namespace pa {
@@ -210,6 +212,28 @@ void launch_plot_centres(const CentreTab* d_tabs, int ntabs, int64_t total_items
   plot_centres_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_tabs, ntabs, total_items);
 }
 
+// Clear the listed ranges with every thread of the grid, eight words per
+// thread and step: chunk c covers words [8c, 8c + 8) of the ranges' flat
+// index space and may cross from one range into the next.
+__device__ __forceinline__ void clear_ranges(const ZeroRange* __restrict__ zr, int nzero,
+                                             int64_t zero_words) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = gid; c * 8 < zero_words; c += gstride) {
+    int64_t w = c * 8;
+    const int64_t wend = min(zero_words, w + 8);
+    int lo = 0, hi = nzero - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (zr[mid].w0 <= w) lo = mid; else hi = mid - 1;
+    }
+    for (int r = lo; w < wend && r < nzero; ++r) {
+      const int64_t end = min(wend, zr[r].w0 + zr[r].words);
+      for (; w < end; ++w) zr[r].p[w - zr[r].w0] = 0ull;
+    }
+  }
+}
+
 template <int DS, bool EQ, bool YS, bool FULL>
 __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
                                           const float* ytab_w, const float* __restrict__ y32g,
@@ -258,7 +282,8 @@ __device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, f
 
 template <int DS>
 __global__ void __launch_bounds__(kPlotThreads)
-plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstride, int rmax) {
+plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstride, int rmax,
+            const ZeroRange* __restrict__ zr, int nzero, int64_t zero_words) {
   extern __shared__ __align__(16) unsigned char plot_smem[];
   asm volatile("griddepcontrol.launch_dependents;");
   // [rmax][gstride] FP64 row polynomials, [rmax][gstride] FP32 copies,
@@ -327,6 +352,9 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   // visible past this point; nothing global is read or written before it but
   // the job descriptors and coefficients
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the later contractions' result buffers that start at zero (each block a
+  // share; a block's share is small next to its plot tile)
+  if (zero_words > 0) clear_ranges(zr, nzero, zero_words);
   if (hoisted) {
     if (ysmem)
       for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = J->y32[i];
@@ -441,7 +469,7 @@ cudaError_t probe_kernel_image() {
 
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, int64_t max_tile_words,
-                 cudaStream_t s) {
+                 const ZeroRange* d_zero, int nzero, int64_t zero_words, cudaStream_t s) {
   if (total_tiles <= 0) return;
   const int ycap = max_res_last <= kYTabCap ? max_res_last : 0;
   const int gstride = max_degree + 1, rmax = max_rows_per_tile;
@@ -467,7 +495,8 @@ void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_
   do {                                                                                       \
     cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                          (int)smem);                                                         \
-    cudaLaunchKernelEx(&cfg, plot_kernel<DD>, d_jobs, njobs, ycap, gstride, rmax);           \
+    cudaLaunchKernelEx(&cfg, plot_kernel<DD>, d_jobs, njobs, ycap, gstride, rmax, d_zero,    \
+                       nzero, zero_words);                                                   \
   } while (0)
   switch (common_degree) {
     case 1: PA_PLOT(1); break;

@@ -81,12 +81,17 @@ def random_order(system, rng, max_bits=1 << 26, tries=50):
 
 
 def collect_logs(engine, systems, orders_per_system=4, seed=0, max_bits=1 << 26):
-    """Features and log2(us)/8 targets from the greedy order, the left-to-right
-    order and random orders of every system."""
+    """Features and log2(us)/8 targets from the greedy order, the
+    least-naive-cost order, the left-to-right order and random orders of
+    every system."""
     rng = np.random.default_rng(seed)
     X, T, D = [], [], []
     for sy in systems:
+        from . import pa_plan_order
         runs = [("greedy", None), ("left", None)]
+        p_opt, _, peak = pa_plan_order(sy.axes, sy.rels, sy.exposed, "optimal")
+        if peak <= max_bits:
+            runs.append(("given", p_opt))
         for _ in range(orders_per_system):
             p = random_order(sy, rng, max_bits)
             if p is not None:

@@ -101,32 +101,62 @@ def small_networks(n, seed):
                              res_choices=(48, 64, 96))
 
 
+def order_matters_networks(seed, n, min_ratio=2.0):
+    """Random networks at 128 pixels whose greedy order costs at least
+    `min_ratio` times the least naive cost (Sec. 3.5): networks where the
+    choice of order matters."""
+    nets = L.usable_networks(W.random_networks(200, seed=seed, res_choices=(128,)),
+                             max_peak_bits=1 << 26)
+    out = []
+    for sy in nets:
+        _, g, _ = pa.pa_plan_order(sy.axes, sy.rels, sy.exposed, "greedy")
+        _, o, _ = pa.pa_plan_order(sy.axes, sy.rels, sy.exposed, "optimal")
+        if g >= min_ratio * o:
+            out.append(sy)
+    return out[:n]
+
+
+def measured_us(eng, sy, reps=3, **kw):
+    """Least over reps of the summed join times of one solve (one launch per join)."""
+    best = None
+    for _ in range(reps):
+        _, us, _, _ = eng.log_joins(sy, **kw)
+        t = float(us.sum())
+        best = t if best is None else min(best, t)
+    return best
+
+
 def test_learned_order_bit_exact_and_gain(eng, orc):
-    """Train on solver logs of training networks, then solve held-out networks
-    with the learned order: identical bits to the oracle, and the learned order
-    is never predicted slower than greedy (the judge), and measured no slower
-    than greedy by more than 15 % in total."""
-    train = small_networks(24, 101)
+    """Train on solver logs of training networks, log the greedy order of the
+    held-out networks (the judge's measured side), then solve them with the
+    learned order: identical bits to the oracle, and a measured total join
+    time strictly below greedy's."""
+    train = L.usable_networks(W.random_networks(24, seed=101, res_choices=(64, 128)),
+                              max_peak_bits=1 << 26)
     X, T, D = L.collect_logs(eng, train, orders_per_system=3, seed=1)
     m = pa.CostModel(eng, hidden=128, nlayers=3, seed=5)
     hist = m.train(X, T, epochs=120, batch=256, lr=2e-3)
     assert hist[-1] < hist[0]
-    held = small_networks(12, 202)
-    orders, learned, pred = eng.plan_learned(m, held)
-    assert np.all(pred[:, 0] <= pred[:, 1] * (1 + 1e-6))
+    held = order_matters_networks(404, 8)
+    assert len(held) >= 6
+    for sy in held:
+        eng.log_joins(sy)
+    eng.sync()
+    orders, learned, judge = eng.plan_learned(m, held)
+    assert np.all(judge[:, 0] <= judge[:, 1] * (1 + 1e-6))
+    assert sum(learned) >= 1
     t_learned = t_greedy = 0.0
     for sy, pairs in zip(held, orders):
         out, _ = eng.solve(sy, order="learned", model=m)
         eng.sync()
         want = orc.solve(sy.axes, sy.rels, sy.exposed).data
         assert np.array_equal(out.to_numpy(), want), sy.name
-        _, us_l, _, _ = eng.log_joins(sy, order="given", pairs=pairs)
-        _, us_g, _, _ = eng.log_joins(sy, order="greedy")
-        t_learned += float(us_l.sum())
-        t_greedy += float(us_g.sum())
-    print(f"learned orders kept for {sum(learned)}/{len(held)} networks; "
-          f"measured join time learned {t_learned:.1f} us vs greedy {t_greedy:.1f} us")
-    assert t_learned <= 1.15 * t_greedy
+        t_learned += measured_us(eng, sy, order="given", pairs=pairs)
+        t_greedy += measured_us(eng, sy, order="greedy")
+    print(f"learned orders kept for {sum(learned)}/{len(held)} networks; measured join time "
+          f"learned {t_learned:.1f} us vs greedy {t_greedy:.1f} us "
+          f"({t_greedy / t_learned:.2f}x)")
+    assert t_learned < t_greedy
     m.close()
 
 

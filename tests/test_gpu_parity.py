@@ -226,10 +226,27 @@ def test_solve_chain_ragged(eng, orc, res):
 def test_solve_orders_identical(eng, orc):
     sysm = W.chain(res=150, nrel=6, seed=99)
     want = orc.solve(sysm.axes, sysm.rels, sysm.exposed).data
-    for order, pairs in (("greedy", None), ("left", None),
+    for order, pairs in (("greedy", None), ("left", None), ("optimal", None),
                          ("given", [(4, 5), (2, 3), (0, 1), (6, 7), (8, 9)])):
         out, _ = eng.solve(sysm, order=order, pairs=pairs)
         check_same(out, want, order)
+
+
+def test_solve_optimal_order_networks(eng, orc):
+    """The least-naive-cost tree (Sec. 3.5) on random networks, single solves
+    and one batch: the same bits as the oracle's own order (Sec. 3.3,
+    associativity), for a naive cost never above greedy's."""
+    nets = W.random_networks(6, seed=515, nvars_range=(8, 12), nrel_range=(10, 18),
+                             res_choices=(48, 64, 100))
+    outs, st = eng.solve_batch(nets, order="optimal")
+    _, st_g = eng.solve_batch(nets, order="greedy")
+    eng.sync()
+    assert st["pixel_ops_dense"] <= st_g["pixel_ops_dense"]
+    for o, sy in zip(outs, nets):
+        want = orc.solve(sy.axes, sy.rels, sy.exposed).data
+        check_same(o, want, sy.name)
+        single, _ = eng.solve(sy, order="optimal")
+        check_same(single, want, sy.name + " single")
 
 
 @pytest.mark.parametrize("res", [16, 50, 64])
