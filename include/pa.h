@@ -89,11 +89,51 @@ typedef struct {
   int32_t res;
 } pa_axis;
 
-/* A polynomial relation over `arity` ports; port p reads variable vars[p].
- * A variable may fill several ports (a loop in the wiring diagram, Sec. 3.1):
- * the relation is then plotted on the diagonal.  `coeffs` is a HOST pointer to
- * C(arity + degree, degree) doubles in graded lex order.  eps >= 0 is the
- * tolerance; eps < 0 asks the library for a valid one (pa_valid_tolerance). */
+/* ------------------------------------------------------ expression relations
+ * A relation may also be any expression built from the ports with the
+ * operations below (the paper's own examples mix polynomials with |.|, cos,
+ * ln, tan, cosh, exp and reciprocals: Sec. 2.1 and Sec. 2.4).  The expression
+ * is a postfix program over a stack of doubles: each instruction is one
+ * int32, op | (arg << 8) with a signed 24-bit arg.
+ *   PA_X_CONST  push consts[arg]        PA_X_VAR   push port arg's coordinate
+ *   PA_X_ADD, PA_X_SUB, PA_X_MUL, PA_X_DIV, PA_X_POW: pop b, pop a, push a op b
+ *   PA_X_NEG, PA_X_ABS, PA_X_SQRT, PA_X_EXP, PA_X_LOG (natural), PA_X_SIN,
+ *   PA_X_COS, PA_X_TAN, PA_X_SINH, PA_X_COSH, PA_X_TANH, PA_X_ATAN: pop a,
+ *   push op(a)
+ *   PA_X_POWI   pop a, push a^arg for an integer arg: |arg| - 1 products from
+ *               a, left to right, then 1 / that for arg < 0 (arg = 0: 1.0)
+ * A program must leave exactly one value; it may not pop an empty stack or
+ * hold more than PA_EXPR_MAX_STACK values.  Every operation is evaluated in
+ * IEEE double precision: +, -, *, / and sqrt correctly rounded, the others by
+ * the CUDA math library (results may differ from another library's in the
+ * last bits; a pixel whose |f| lies within that difference of eps may then
+ * be decided differently).  Non-finite results turn the pixel off as for
+ * polynomials.  An expression relation needs its own eps >= 0: the library
+ * computes valid tolerances for polynomials only. */
+#define PA_EXPR_MAX_OPS 256
+#define PA_EXPR_MAX_STACK 16
+typedef enum {
+  PA_X_CONST = 0, PA_X_VAR = 1, PA_X_ADD = 2, PA_X_SUB = 3, PA_X_MUL = 4, PA_X_DIV = 5,
+  PA_X_NEG = 6, PA_X_ABS = 7, PA_X_SQRT = 8, PA_X_EXP = 9, PA_X_LOG = 10, PA_X_SIN = 11,
+  PA_X_COS = 12, PA_X_TAN = 13, PA_X_SINH = 14, PA_X_COSH = 15, PA_X_TANH = 16,
+  PA_X_ATAN = 17, PA_X_POWI = 18, PA_X_POW = 19
+} pa_expr_op;
+
+typedef struct {
+  int32_t nops;
+  const int32_t* ops;   /* HOST pointer: nops instructions */
+  int32_t nconsts;
+  const double* consts; /* HOST pointer: nconsts doubles */
+} pa_expr;
+
+/* A relation over `arity` ports; port p reads variable vars[p].  A variable
+ * may fill several ports (a loop in the wiring diagram, Sec. 3.1): the
+ * relation is then plotted on the diagonal.  With expr == NULL the relation is
+ * a polynomial: `coeffs` is a HOST pointer to C(arity + degree, degree)
+ * doubles in graded lex order.  With expr != NULL the relation is that
+ * expression of the ports (degree and coeffs are ignored).  eps >= 0 is the
+ * tolerance; eps < 0 asks the library for a valid one (pa_valid_tolerance;
+ * polynomials only). */
 typedef struct {
   int32_t arity;
   int32_t vars[PA_MAX_DIM];
@@ -101,6 +141,7 @@ typedef struct {
   const double* coeffs;
   int32_t kind;
   double eps;
+  const pa_expr* expr;
 } pa_relation;
 
 /* A bit-packed Boolean array on the device (layout above).  `words` holds
@@ -226,9 +267,10 @@ pa_status pa_set_rates(pa_ctx* ctx, const pa_rates* rates);
 /* Number of uint64 words of a pa_array of this shape (host only, no GPU). */
 int64_t pa_array_words(int32_t ndim, const int32_t* res);
 
-/* A valid tolerance for `rel` on the box `axes` (indexed by variable id), Sec.
- * 3.2 Eq. (continuity): eps with |f(x) - f(c)| <= eps whenever x lies in the
- * pixel centred at c.  Computed on the host as
+/* A valid tolerance for the polynomial relation `rel` on the box `axes`
+ * (indexed by variable id), Sec. 3.2 Eq. (continuity): eps with
+ * |f(x) - f(c)| <= eps whenever x lies in the pixel centred at c (an
+ * expression relation returns PA_ERR_UNSUPPORTED).  Computed on the host as
  *   (1 + 2^-30) * sum_p S_p * delta_p / 2,
  *   S_p = sum_e |c_e| e_p M_p^(e_p - 1) prod_{q != p} M_q^(e_q),  M_q = max(|lo_q|, |hi_q|),
  * in a fixed order (ports ascending, monomials in graded lex order, factors left

@@ -15,6 +15,7 @@ resolutions of the array's variables, axes in the order of ``Arr.vars``.
 Functions (passages of Spivak et al., arXiv 1609.00061):
   valid_tolerance   Sec. 3.2, Eq. (continuity): a valid tolerance for a polynomial
   plot              Sec. 3.2, sample-in-center plot
+  eval_expr, plot_expr  expression relations (Sec. 2.1, Sec. 2.4) and their plot
   gam               Sec. 3.3, Algorithm 1 (all arrays at once; tiny grids)
   contract          Sec. 3.3 Eq. (GAM) on one two-array cluster (Sec. 3.5)
   reduce            Eq. (GAM) with one array: OR over the dropped variables
@@ -76,6 +77,11 @@ def _L():
         lib.or_contract_pair.restype = ctypes.c_int
         lib.or_contract_pair.argtypes = [ctypes.c_int, i32p, u8p, ctypes.c_int, i32p, u8p,
                                          ctypes.c_int, i32p, i32p, u8p]
+        lib.or_eval_expr.restype = ctypes.c_double
+        lib.or_eval_expr.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p]
+        lib.or_plot_expr.restype = ctypes.c_int
+        lib.or_plot_expr.argtypes = [ctypes.c_int, ctypes.c_int, i32p, f64p, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, f64p, f64p, i32p, u8p]
         lib.or_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -147,10 +153,36 @@ def plot(degree: int, coeffs, kind: int, eps: float, lo, hi, res, strict: bool =
     return out
 
 
+def eval_expr(ops, consts, x, with_mag: bool = False):
+    """An expression relation's value at the point x (one coordinate per port);
+    with_mag: also the largest magnitude of any value the program pushed."""
+    o, op = _i32(ops)
+    c, cp = _f64(consts if len(consts) else [0.0])
+    xx, xp = _f64(x)
+    mag = ctypes.c_double()
+    f = float(_L().or_eval_expr(len(o), op, cp, xp, ctypes.byref(mag)))
+    return (f, mag.value) if with_mag else f
+
+
+def plot_expr(ops, consts, kind: int, eps: float, lo, hi, res, strict: bool = False) -> np.ndarray:
+    """Sample-in-center plot of an expression relation over its ports."""
+    o, op = _i32(ops)
+    c, cp = _f64(consts if len(consts) else [0.0])
+    l, lp = _f64(lo)
+    h, hp = _f64(hi)
+    r, rp = _i32(res)
+    out = np.zeros(tuple(int(v) for v in r), dtype=np.uint8)
+    rc = _L().or_plot_expr(len(r), len(o), op, cp, int(kind), float(eps), int(bool(strict)), lp, hp,
+                           rp, _u8(out))
+    assert rc == 0
+    return out
+
+
 def relation_eps(rel, axes) -> float:
     """Tolerance of a relation: its own when given (>= 0), else a valid one."""
     if rel.eps >= 0:
         return float(rel.eps)
+    assert getattr(rel, "expr", None) is None, "expression relations carry their own eps"
     lo = [axes[v][0] for v in rel.vars]
     hi = [axes[v][1] for v in rel.vars]
     res = [axes[v][2] for v in rel.vars]
@@ -163,6 +195,9 @@ def plot_relation(rel, axes, strict: bool = False) -> Arr:
     hi = [axes[v][1] for v in rel.vars]
     res = [axes[v][2] for v in rel.vars]
     eps = relation_eps(rel, axes)
+    if getattr(rel, "expr", None) is not None:
+        ops, consts = rel.expr
+        return Arr(plot_expr(ops, consts, rel.kind, eps, lo, hi, res, strict), tuple(rel.vars))
     return Arr(plot(rel.degree, rel.coeffs, rel.kind, eps, lo, hi, res, strict), tuple(rel.vars))
 
 

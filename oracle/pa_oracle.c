@@ -18,6 +18,8 @@
  *   or_valid_tolerance                -- a valid tolerance, Sec. 3.2, Eq. (continuity)
  *   or_plot                           -- sample-in-center plot, Sec. 3.2, Definition
  *                                        of the epsilon-tolerance sample-in-center plot
+ *   or_eval_expr / or_plot_expr       -- expression relations (Sec. 2.1, Sec. 2.4) and
+ *                                        their sample-in-center plot
  *   or_gam                            -- Algorithm 1 (generalized array multiplication)
  *   or_contract_pair                  -- Eq. (GAM) for a two-array cluster (Sec. 3.5)
  *
@@ -251,6 +253,100 @@ int or_plot(int n, int degree, const double* coeffs, int kind, double eps, int s
  * array i is wired to link port_links[off_i + j]; the outer pack's ports are
  * wired to out_links.  Entr^i(e) reads the link value of every port.  Loops run
  * over every entry of Entr(Lambda) exactly as the algorithm states (tiny grids). */
+/* ------------------------------------------------------------- expressions
+ * A relation given as an expression of its ports (the paper's examples in
+ * Sec. 2.1 and Sec. 2.4 use |.|, cos, ln, tan, cosh, exp and reciprocals).
+ * The expression is a postfix program: instruction k is op | (arg << 8) with
+ * a signed arg; op 0 pushes consts[arg], op 1 pushes the coordinate of port
+ * arg, ops 2..5 and 19 pop b then a and push a+b, a-b, a*b, a/b, pow(a, b);
+ * ops 6..17 replace the top a by -a, |a|, sqrt, exp, ln, sin, cos, tan, sinh,
+ * cosh, tanh, atan (C library); op 18 replaces a by a^arg for an integer arg:
+ * a multiplied by itself |arg| - 1 times left to right, then 1 / that when
+ * arg < 0, and 1 when arg = 0.
+ * *mag (when mag is not NULL) receives the largest magnitude of any value
+ * the program pushes: rounding differences between math libraries scale with
+ * it, which is what the parity tests' tolerance at the threshold uses. */
+double or_eval_expr(int nops, const int* ops, const double* consts, const double* x,
+                    double* mag) {
+  double st[64];
+  int sp = 0;
+  double m = 0.0;
+  for (int k = 0; k < nops; ++k) {
+    int op = ops[k] & 0xff;
+    int arg = ops[k] >> 8;
+    double a, b, r;
+    if (op == 0) {
+      r = consts[arg];
+    } else if (op == 1) {
+      r = x[arg];
+    } else if ((op >= 2 && op <= 5) || op == 19) {
+      b = st[--sp];
+      a = st[--sp];
+      if (op == 2) r = a + b;
+      else if (op == 3) r = a - b;
+      else if (op == 4) r = a * b;
+      else if (op == 5) r = a / b;
+      else r = pow(a, b);
+    } else {
+      a = st[--sp];
+      switch (op) {
+        case 6: r = -a; break;
+        case 7: r = fabs(a); break;
+        case 8: r = sqrt(a); break;
+        case 9: r = exp(a); break;
+        case 10: r = log(a); break;
+        case 11: r = sin(a); break;
+        case 12: r = cos(a); break;
+        case 13: r = tan(a); break;
+        case 14: r = sinh(a); break;
+        case 15: r = cosh(a); break;
+        case 16: r = tanh(a); break;
+        case 17: r = atan(a); break;
+        case 18: {
+          int n = arg < 0 ? -arg : arg;
+          r = 1.0;
+          if (n > 0) {
+            r = a;
+            for (int j = 1; j < n; ++j) r = r * a;
+          }
+          if (arg < 0) r = 1.0 / r;
+          break;
+        }
+        default: r = NAN; break;
+      }
+    }
+    st[sp++] = r;
+    if (fabs(r) > m || r != r) m = (r != r) ? INFINITY : fmax(m, fabs(r));
+  }
+  if (mag) *mag = m;
+  return sp == 1 ? st[0] : NAN;
+}
+
+/* Sample-in-center plot of an expression relation over its ports (same pixel
+ * centres and decision as or_plot). */
+int or_plot_expr(int n, int nops, const int* ops, const double* consts, int kind, double eps,
+                 int strict, const double* lo, const double* hi, const int* res, uint8_t* out) {
+  if (n < 1 || n > OR_MAX_DIM || nops < 1) return -1;
+  int64_t total = 1;
+  for (int p = 0; p < n; ++p) total *= res[p];
+  double delta[OR_MAX_DIM];
+  for (int p = 0; p < n; ++p) delta[p] = (hi[p] - lo[p]) / (double)res[p];
+#pragma omp parallel for schedule(static)
+  for (int64_t flat = 0; flat < total; ++flat) {
+    int64_t rest = flat;
+    double x[OR_MAX_DIM];
+    for (int p = n - 1; p >= 0; --p) {
+      int64_t i = rest % res[p];
+      rest /= res[p];
+      double t = (double)i + 0.5;
+      x[p] = lo[p] + t * delta[p];
+    }
+    double f = or_eval_expr(nops, ops, consts, x, NULL);
+    out[flat] = (uint8_t)decide(f, kind, eps, strict);
+  }
+  return 0;
+}
+
 int or_gam(int nlinks, const int* link_res, int narr, const int* ndims,
            const int* port_links, const uint8_t* const* arrays, int nout,
            const int* out_links, uint8_t* out) {

@@ -19,7 +19,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native
-from ._native import PaArray, PaAxis, PaOptions, PaRates, PaRelation, PaStats, PaSystem
+from ._native import (PaArray, PaAxis, PaExpr, PaOptions, PaRates, PaRelation, PaStats,
+                      PaSystem)
 
 PA_OK = 0
 STATUS = {0: "PA_OK", 1: "PA_ERR_INVALID_ARG", 2: "PA_ERR_UNSUPPORTED", 3: "PA_ERR_TOO_LARGE",
@@ -53,8 +54,10 @@ def _axes(axes):
 
 
 def _relations(rels):
+    """Marshal relations; returns (array, coefficient arrays).  The expression
+    programs stay referenced by the array's `_keep` attribute."""
     arr = (PaRelation * len(rels))()
-    keep = []
+    keep, extra = [], []
     for i, r in enumerate(rels):
         c = np.ascontiguousarray(r.coeffs, dtype=np.float64)
         keep.append(c)
@@ -65,6 +68,18 @@ def _relations(rels):
         arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         arr[i].kind = int(r.kind)
         arr[i].eps = float(r.eps)
+        ex = getattr(r, "expr", None)
+        if ex is not None:
+            ops = np.ascontiguousarray(ex[0], dtype=np.int32)
+            consts = np.ascontiguousarray(ex[1], dtype=np.float64)
+            pe = PaExpr()
+            pe.nops = len(ops)
+            pe.ops = ops.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            pe.nconsts = len(consts)
+            pe.consts = consts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            extra.append((ops, consts, pe))
+            arr[i].expr = ctypes.pointer(pe)
+    arr._keep = extra
     return arr, keep
 
 
@@ -201,7 +216,8 @@ def _network_args(axes, rels, exposed) -> _NetArgs:
     # contiguous float64 array (no converted copy)
     n.coeffs = [k if k is r.coeffs else None for k, r in zip(keep, rels)]
     n.c_exposed = _i32(exposed)
-    if all(c is not None for c in n.coeffs):
+    if all(c is not None for c in n.coeffs) and all(getattr(r, "expr", None) is None
+                                                    for r in rels):
         _last_net = n
     else:
         n.coeffs = keep

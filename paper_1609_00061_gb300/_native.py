@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
 _ROOT = os.path.dirname(_HERE)
 INCLUDE = os.path.join(_ROOT, "include")
 
-CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu", "mma.cu"]
+CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu", "mma.cu", "expr.cu"]
 CPP_SOURCES = ["planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -86,9 +86,15 @@ class PaAxis(ctypes.Structure):
     _fields_ = [("lo", c_f64), ("hi", c_f64), ("res", c_i32)]
 
 
+class PaExpr(ctypes.Structure):
+    _fields_ = [("nops", c_i32), ("ops", ctypes.POINTER(c_i32)), ("nconsts", c_i32),
+                ("consts", ctypes.POINTER(c_f64))]
+
+
 class PaRelation(ctypes.Structure):
     _fields_ = [("arity", c_i32), ("vars", c_i32 * MAX_DIM), ("degree", c_i32),
-                ("coeffs", ctypes.POINTER(c_f64)), ("kind", c_i32), ("eps", c_f64)]
+                ("coeffs", ctypes.POINTER(c_f64)), ("kind", c_i32), ("eps", c_f64),
+                ("expr", ctypes.POINTER(PaExpr))]
 
 
 class PaArray(ctypes.Structure):

@@ -87,7 +87,7 @@ bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end()
 
 // ------------------------------------------------------------ program
 enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
-              OP_MMA, OP_CENTRES };
+              OP_MMA, OP_CENTRES, OP_PLOT_EXPR };
 
 struct Op {
   OpKind kind;
@@ -109,6 +109,7 @@ const char* op_name(const Op& op) {
   switch (op.kind) {
     case OP_PLOT: return "plot_kernel";
     case OP_CENTRES: return "plot_centres_kernel";
+    case OP_PLOT_EXPR: return "plot_expr_kernel";
     case OP_MEMSET: return "memset";
     case OP_RESHAPE:
       return op.rd.mode == kReshapeTranspose ? "reshape_transpose_kernel"
@@ -731,8 +732,40 @@ void check_axes(pa_ctx* ctx, int32_t nvars, const pa_axis* axes) {
   }
 }
 
+// An expression's program: valid instructions and arguments, a stack that
+// never underflows or exceeds PA_EXPR_MAX_STACK and ends with one value.
+void check_expr(pa_ctx* ctx, const pa_expr& e, int arity) {
+  PA_CHECK_ARG(e.nops >= 1 && e.nops <= PA_EXPR_MAX_OPS && e.ops, "expression: 1..256 instructions");
+  PA_CHECK_ARG(e.nconsts >= 0 && e.nconsts <= PA_EXPR_MAX_OPS && (e.nconsts == 0 || e.consts),
+               "expression: 0..256 constants");
+  for (int i = 0; i < e.nconsts; ++i)
+    PA_CHECK_ARG(!isnan(e.consts[i]), "expression: constants must not be NaN");
+  int sp = 0;
+  for (int k = 0; k < e.nops; ++k) {
+    const int op = e.ops[k] & 0xff, arg = e.ops[k] >> 8;
+    PA_CHECK_ARG(op <= PA_X_POW, "expression: unknown instruction");
+    if (op == PA_X_CONST) PA_CHECK_ARG(arg >= 0 && arg < e.nconsts, "expression: constant index");
+    if (op == PA_X_VAR) PA_CHECK_ARG(arg >= 0 && arg < arity, "expression: port index");
+    if (op == PA_X_POWI) PA_CHECK_ARG(arg >= -64 && arg <= 64, "expression: integer power in -64..64");
+    const int pops = (op == PA_X_CONST || op == PA_X_VAR) ? 0
+                     : ((op >= PA_X_ADD && op <= PA_X_DIV) || op == PA_X_POW) ? 2 : 1;
+    PA_CHECK_ARG(sp >= pops, "expression: stack underflow");
+    sp += 1 - pops;
+    PA_CHECK_ARG(sp <= PA_EXPR_MAX_STACK, "expression: more than 16 stack values");
+  }
+  PA_CHECK_ARG(sp == 1, "expression: must leave exactly one value");
+}
+
 void check_relation(pa_ctx* ctx, const pa_relation& r, int32_t nvars) {
   PA_CHECK_ARG(r.arity >= 1 && r.arity <= PA_MAX_DIM, "relation arity must be in 1..8");
+  if (r.expr) {
+    check_expr(ctx, *r.expr, r.arity);
+    PA_CHECK_ARG(r.kind == PA_EQ || r.kind == PA_LE || r.kind == PA_LT, "relation kind");
+    PA_CHECK_ARG(r.eps >= 0 && r.eps < INFINITY, "expression relation: eps must be >= 0 and finite");
+    for (int p = 0; p < r.arity; ++p)
+      PA_CHECK_ARG(r.vars[p] >= 0 && r.vars[p] < nvars, "relation variable out of range");
+    return;
+  }
   PA_CHECK_ARG(r.degree >= 0 && r.degree <= PA_MAX_DEGREE, "relation degree must be in 0..16");
   PA_CHECK_ARG(r.coeffs != nullptr, "relation coefficients: null pointer");
   PA_CHECK_ARG(r.kind == PA_EQ || r.kind == PA_LE || r.kind == PA_LT, "relation kind");
@@ -752,7 +785,7 @@ std::vector<int> distinct_vars(const pa_relation& r) {
 }
 
 double relation_eps(const pa_relation& r, const pa_axis* axes) {
-  if (r.eps >= 0) return r.eps;
+  if (r.eps >= 0 || r.expr) return r.eps;
   double lo[kMaxDim], hi[kMaxDim];
   int32_t res[kMaxDim];
   for (int p = 0; p < r.arity; ++p) {
@@ -783,9 +816,86 @@ struct PlotReq {
   uint64_t* direct;  // plot straight into this array (pa_plot), else workspace
 };
 
-// Every requested plot in two launches: the FP32 centre tables of the last
-// ports (once per distinct axis, not once per block), then the plot itself.
+std::vector<BitArr> plot_poly(Builder& bd, const std::vector<PlotReq>& reqs);
+
+// Every requested plot: the expression relations in one launch (first, so
+// that the polynomial plot launch stays right before the contractions), the
+// polynomial ones in the two launches of plot_poly.  Arrays come back in the
+// order of `reqs`.
 std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
+  std::vector<BitArr> plots(reqs.size());
+  std::vector<PlotReq> poly;
+  std::vector<size_t> poly_at;
+  std::vector<ExprJob> ejobs;
+  std::vector<size_t> prog_off, const_off;
+  int64_t words = 0;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    const pa_relation& r = *reqs[i].rel;
+    if (!r.expr) {
+      poly.push_back(reqs[i]);
+      poly_at.push_back(i);
+      continue;
+    }
+    const pa_axis* axes = reqs[i].axes;
+    const std::vector<int> dv = distinct_vars(r);
+    BitArr a;
+    a.ndim = (int)dv.size();
+    a.inner = 1;
+    for (int k = 0; k < a.ndim; ++k) {
+      a.vars[k] = dv[k];
+      a.res[k] = axes[dv[k]].res;
+    }
+    a.w = reqs[i].direct ? reqs[i].direct : bd.alloc_words(a.words());
+    plots[i] = a;
+    ExprJob J;
+    memset(&J, 0, sizeof J);
+    J.out = a.w;
+    J.arity = r.arity;
+    J.kind = r.kind;
+    J.strict = reqs[i].strict;
+    J.eps = r.eps;
+    J.ndim = a.ndim;
+    for (int k = 0; k < a.ndim; ++k) J.res[k] = (int32_t)a.res[k];
+    for (int p = 0; p < r.arity; ++p) {
+      const pa_axis& ax = axes[r.vars[p]];
+      J.port_axis[p] = axis_of(a, r.vars[p]);
+      J.lo[p] = ax.lo;
+      J.delta[p] = (ax.hi - ax.lo) / (double)ax.res;
+    }
+    J.nops = r.expr->nops;
+    J.nrows = a.nrows();
+    J.row_words = a.row_words();
+    J.word0 = words;
+    words += a.words();
+    prog_off.push_back(bd.put(r.expr->ops, (size_t)r.expr->nops));
+    const_off.push_back(bd.put(r.expr->consts, (size_t)r.expr->nconsts));
+    ejobs.push_back(J);
+    bd.st.pixels_plotted += (double)a.bits();
+    bd.st.n_plots++;
+  }
+  if (!ejobs.empty()) {
+    for (size_t k = 0; k < ejobs.size(); ++k) {
+      ejobs[k].prog = reinterpret_cast<const int32_t*>(bd.dev(prog_off[k]));
+      ejobs[k].consts = reinterpret_cast<const double*>(bd.dev(const_off[k]));
+    }
+    Op op;
+    op.kind = OP_PLOT_EXPR;
+    op.off0 = bd.put(ejobs.data(), ejobs.size(), 64);
+    op.n = (int)ejobs.size();
+    op.count = words;
+    bd.ops.push_back(op);
+  }
+  if (!poly.empty()) {
+    const std::vector<BitArr> pp = plot_poly(bd, poly);
+    for (size_t k = 0; k < pp.size(); ++k) plots[poly_at[k]] = pp[k];
+  }
+  return plots;
+}
+
+// The polynomial relations' plots in two launches: the FP32 centre tables of
+// the last ports (once per distinct axis, not once per block), then the plot
+// itself.
+std::vector<BitArr> plot_poly(Builder& bd, const std::vector<PlotReq>& reqs) {
   const int nrel = (int)reqs.size();
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
@@ -1117,6 +1227,9 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
                     op.i1, op.i2, op.i3, op.m, reinterpret_cast<const ZeroRange*>(blob + op.off1),
                     (int)op.nw, op.zw, s);
         break;
+      case OP_PLOT_EXPR:
+        launch_plot_expr(reinterpret_cast<const ExprJob*>(blob + op.off0), op.n, op.count, s);
+        break;
       case OP_CENTRES:
         launch_plot_centres(reinterpret_cast<const CentreTab*>(blob + op.off0), op.n, op.count, s);
         break;
@@ -1288,7 +1401,15 @@ std::vector<char> solve_key(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int
     put_val(k, r.degree);
     put_val(k, r.kind);
     put_val(k, r.eps);
-    put_bytes(k, r.coeffs, sizeof(double) * coeff_count(r.arity, r.degree));
+    if (r.expr) {
+      put_val(k, r.expr->nops);
+      put_bytes(k, r.expr->ops, sizeof(int32_t) * r.expr->nops);
+      put_val(k, r.expr->nconsts);
+      put_bytes(k, r.expr->consts, sizeof(double) * r.expr->nconsts);
+    } else {
+      put_val(k, (int32_t)-1);
+      put_bytes(k, r.coeffs, sizeof(double) * coeff_count(r.arity, r.degree));
+    }
   }
   put_val(k, nexposed);
   put_bytes(k, exposed, sizeof(int32_t) * nexposed);
@@ -1385,9 +1506,47 @@ double nest_host(int k, int rem, const double*& cp, const double* x) {
 // Fraction of pixels a plot turns on, estimated from 512 sampled pixel centres:
 // for f = 0 by a Gaussian kernel estimate of the density of f(c) at 0 (times
 // the width 2 eps of the accepted band), for f <= 0 / f < 0 by counting.
+// An expression relation at one point (host; only density estimates use it,
+// so the math library's last bits do not matter here).
+double expr_host(const pa_expr& e, const double* x) {
+  double st[PA_EXPR_MAX_STACK];
+  int sp = 0;
+  for (int k = 0; k < e.nops; ++k) {
+    const int op = e.ops[k] & 0xff, arg = e.ops[k] >> 8;
+    if (op == PA_X_CONST) { st[sp++] = e.consts[arg]; continue; }
+    if (op == PA_X_VAR) { st[sp++] = x[arg]; continue; }
+    if ((op >= PA_X_ADD && op <= PA_X_DIV) || op == PA_X_POW) {
+      const double b = st[--sp], a = st[sp - 1];
+      st[sp - 1] = op == PA_X_ADD ? a + b : op == PA_X_SUB ? a - b : op == PA_X_MUL ? a * b
+                   : op == PA_X_DIV ? a / b : pow(a, b);
+      continue;
+    }
+    const double a = st[sp - 1];
+    double r = NAN;
+    switch (op) {
+      case PA_X_NEG: r = -a; break;
+      case PA_X_ABS: r = fabs(a); break;
+      case PA_X_SQRT: r = sqrt(a); break;
+      case PA_X_EXP: r = exp(a); break;
+      case PA_X_LOG: r = log(a); break;
+      case PA_X_SIN: r = sin(a); break;
+      case PA_X_COS: r = cos(a); break;
+      case PA_X_TAN: r = tan(a); break;
+      case PA_X_SINH: r = sinh(a); break;
+      case PA_X_COSH: r = cosh(a); break;
+      case PA_X_TANH: r = tanh(a); break;
+      case PA_X_ATAN: r = atan(a); break;
+      case PA_X_POWI: r = pow(a, (double)arg); break;
+    }
+    st[sp - 1] = r;
+  }
+  return st[0];
+}
+
 double estimate_density(const pa_relation& r, const pa_axis* axes, double eps) {
   const int S = 512;
-  std::vector<int64_t> ord = nest_order(r.arity, r.degree);
+  std::vector<int64_t> ord;
+  if (!r.expr) ord = nest_order(r.arity, r.degree);
   std::vector<double> nc(ord.size());
   for (size_t k = 0; k < ord.size(); ++k) nc[k] = r.coeffs[ord[k]];
   std::vector<double> f(S);
@@ -1400,20 +1559,29 @@ double estimate_density(const pa_relation& r, const pa_axis* axes, double eps) {
       const int64_t idx = (int64_t)(mix64(seed + (uint64_t)i * 16 + p) % (uint64_t)ax.res);
       x[p] = ax.lo + ((double)idx + 0.5) * ((ax.hi - ax.lo) / (double)ax.res);
     }
-    const double* cp = nc.data();
-    f[i] = nest_host(r.arity - 1, r.degree, cp, x);
+    if (r.expr) {
+      f[i] = expr_host(*r.expr, x);
+    } else {
+      const double* cp = nc.data();
+      f[i] = nest_host(r.arity - 1, r.degree, cp, x);
+    }
   }
+  // non-finite values (undefined points) are off and stay out of the estimate
+  f.erase(std::remove_if(f.begin(), f.end(), [](double v) { return !std::isfinite(v); }), f.end());
+  if (f.empty()) return 1e-6;
   int direct = 0;
   for (double v : f)
     direct += (r.kind == PA_EQ) ? (fabs(v) <= eps) : (v <= eps);
   double est = (double)direct / S;
   if (r.kind == PA_EQ) {
+    // the kernel estimate over the finite samples, scaled by their share
+    const double n = (double)f.size();
     double mean = 0, var = 0;
     for (double v : f) mean += v;
-    mean /= S;
+    mean /= n;
     for (double v : f) var += (v - mean) * (v - mean);
-    const double sd = sqrt(var / S);
-    const double h = std::max(1e-300, 1.06 * sd * pow((double)S, -0.2));
+    const double sd = sqrt(var / n);
+    const double h = std::max(1e-300, 1.06 * sd * pow(n, -0.2));
     double acc = 0;
     for (double v : f) acc += exp(-0.5 * (v / h) * (v / h));
     const double pdf0 = acc / (S * h * sqrt(2.0 * M_PI));
@@ -1533,6 +1701,12 @@ uint64_t relation_key(const pa_relation& r, const pa_axis* axes) {
     addd(a.lo);
     addd(a.hi);
     add((uint64_t)a.res << 8 | (uint64_t)p);
+  }
+  if (r.expr) {
+    add(0xE1u);
+    for (int k = 0; k < r.expr->nops; ++k) add((uint64_t)(uint32_t)r.expr->ops[k]);
+    for (int k = 0; k < r.expr->nconsts; ++k) addd(r.expr->consts[k]);
+    return h;
   }
   const int64_t nc = coeff_count(r.arity, r.degree);
   for (int64_t i = 0; i < nc; ++i) addd(r.coeffs[i]);
@@ -1998,6 +2172,7 @@ pa_status pa_valid_tolerance(const pa_relation* rel, const pa_axis* axes, int32_
   try {
     PA_CHECK_ARG(rel && eps_out, "null pointer");
     check_axes(ctx, nvars, axes);
+    if (rel->expr) return PA_ERR_UNSUPPORTED;
     check_relation(ctx, *rel, nvars);
     pa_relation r = *rel;
     r.eps = -1.0;

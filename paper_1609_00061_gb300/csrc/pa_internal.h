@@ -56,6 +56,24 @@ struct CentreTab {
   int64_t item0;  // first item of this table in the centre-table launch
   int64_t res;
 };
+// One expression relation to plot (expr.cu): the postfix program and its
+// constants on the device, the pixel grid as for PlotJob; word0 is the first
+// word of this job in the launch's flat word space.
+struct ExprJob {
+  const int32_t* prog;
+  const double* consts;
+  uint64_t* out;
+  double lo[kMaxDim];
+  double delta[kMaxDim];
+  double eps;
+  int64_t nrows, row_words, word0;
+  int32_t nops, arity, kind, strict, ndim;
+  int32_t res[kMaxDim];
+  int32_t port_axis[kMaxDim];
+};
+// Every expression plot of a call in one launch, one thread per output word.
+void launch_plot_expr(const ExprJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s);
+
 // A range of words to clear: words [w0, w0 + words) of the launch's flat
 // index space are p[0 .. words).
 struct ZeroRange {

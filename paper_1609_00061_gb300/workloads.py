@@ -68,17 +68,104 @@ def coeff_count(n: int, degree: int) -> int:
 
 @dataclass
 class Relation:
-    """f(x_vars) S 0 with f a polynomial; S is =, <= or < by ``kind``."""
+    """f(x_vars) S 0 with f a polynomial (coefficients in graded lex order) or,
+    when ``expr`` is given, an expression program (see ``Ex``); S is =, <= or <
+    by ``kind``."""
     vars: tuple
     degree: int
     coeffs: np.ndarray
     kind: int = KIND_EQ
-    eps: float = -1.0          # < 0: the solver derives a valid tolerance
+    eps: float = -1.0          # < 0: the solver derives a valid tolerance (polynomials)
+    expr: tuple = None         # (int32 instructions, float64 constants) or None
 
     def __post_init__(self):
         self.vars = tuple(int(v) for v in self.vars)
         self.coeffs = np.ascontiguousarray(self.coeffs, dtype=np.float64)
-        assert len(self.coeffs) == coeff_count(len(self.vars), self.degree)
+        if self.expr is None:
+            assert len(self.coeffs) == coeff_count(len(self.vars), self.degree)
+        else:
+            ops, consts = self.expr
+            self.expr = (np.ascontiguousarray(ops, dtype=np.int32),
+                         np.ascontiguousarray(consts, dtype=np.float64))
+
+
+# ------------------------------------------------------ expression programs
+# Instruction codes of the postfix expression programs (include/pa.h, pa_expr).
+X_CONST, X_VAR, X_ADD, X_SUB, X_MUL, X_DIV, X_NEG, X_ABS, X_SQRT, X_EXP, X_LOG = range(11)
+X_SIN, X_COS, X_TAN, X_SINH, X_COSH, X_TANH, X_ATAN, X_POWI, X_POW = range(11, 20)
+
+
+class Ex:
+    """An expression of a relation's ports, built with Python operators and the
+    functions below, written out as the postfix program the library runs.
+    Only the program is built here; nothing is evaluated.
+
+        x, y = Ex.port(0), Ex.port(1)
+        rel = expr_relation((vx, vy), x ** 2 + 3 * abs_(x - y) - 5, eps=0.05)
+    """
+
+    def __init__(self, code):
+        self.code = code          # list of (op, arg) with constants as floats
+
+    @staticmethod
+    def port(p):
+        return Ex([(X_VAR, int(p))])
+
+    @staticmethod
+    def const(c):
+        return Ex([(X_CONST, float(c))])
+
+    @staticmethod
+    def wrap(v):
+        return v if isinstance(v, Ex) else Ex.const(v)
+
+    def _bin(self, other, op, swap=False):
+        a, b = (Ex.wrap(other), self) if swap else (self, Ex.wrap(other))
+        return Ex(a.code + b.code + [(op, 0)])
+
+    def __add__(self, o): return self._bin(o, X_ADD)
+    def __radd__(self, o): return self._bin(o, X_ADD, True)
+    def __sub__(self, o): return self._bin(o, X_SUB)
+    def __rsub__(self, o): return self._bin(o, X_SUB, True)
+    def __mul__(self, o): return self._bin(o, X_MUL)
+    def __rmul__(self, o): return self._bin(o, X_MUL, True)
+    def __truediv__(self, o): return self._bin(o, X_DIV)
+    def __rtruediv__(self, o): return self._bin(o, X_DIV, True)
+    def __neg__(self): return Ex(self.code + [(X_NEG, 0)])
+
+    def __pow__(self, o):
+        if isinstance(o, int):
+            return Ex(self.code + [(X_POWI, o)])
+        return self._bin(o, X_POW)
+
+    def program(self):
+        """(int32 instructions, float64 constants): op | (arg << 8) per instruction."""
+        consts, ops = [], []
+        for op, arg in self.code:
+            if op == X_CONST:
+                key = np.float64(arg).tobytes()
+                idx = next((i for i, c in enumerate(consts) if np.float64(c).tobytes() == key),
+                           None)
+                if idx is None:
+                    idx = len(consts)
+                    consts.append(arg)
+                arg = idx
+            ops.append(op + 256 * int(arg))
+        return (np.array(ops, dtype=np.int32), np.array(consts, dtype=np.float64))
+
+
+def _fn(op):
+    return lambda e: Ex(Ex.wrap(e).code + [(op, 0)])
+
+
+abs_, sqrt_, exp_, log_, sin_, cos_, tan_ = (_fn(X_ABS), _fn(X_SQRT), _fn(X_EXP), _fn(X_LOG),
+                                             _fn(X_SIN), _fn(X_COS), _fn(X_TAN))
+sinh_, cosh_, tanh_, atan_ = _fn(X_SINH), _fn(X_COSH), _fn(X_TANH), _fn(X_ATAN)
+
+
+def expr_relation(vars_, e: Ex, kind: int = KIND_EQ, eps: float = 0.05) -> Relation:
+    """The relation e(ports) S 0 over the given variables (port p reads vars_[p])."""
+    return Relation(tuple(vars_), 0, np.zeros(1), kind, eps, Ex.wrap(e).program())
 
 
 @dataclass
@@ -126,6 +213,70 @@ def ternary(res: int = 256, lo: float = -2.0, hi: float = 2.0,
     rels = [Relation(w, 3, random_cubic(rng, 3)) for w in wiring]
     axes = [(lo, hi, res)] * 6
     return System(f"ternary_r{res}", axes, rels, (0, 1, 2))
+
+
+def butterfly(res: int = 50, lo: float = -3.0, hi: float = 3.0, eps: float = 0.05,
+              exposed=(0, 3)) -> System:
+    """The butterfly example of Sec. 2.4: variables w, x, y, z (ids 0..3) in
+    [-3, 3) at `res` pixels, (w, z) exposed;
+      cos(ln(z^2 + 1e-3 x)) - x + 1e-5 / z = 0,
+      cosh(w + 1e-3 y) + y + 1e-4 w - 2 = 0,
+      tan(x + y) / ((x - 2)(x + 3) y^2) - 1 = 0.
+    The paper times it at resolution 50 with x and z exposed (exposed=(1, 3))
+    and prints the plot at 125 with (w, z) exposed; it states no tolerance, so
+    eps is a parameter."""
+    w, x, y, z = (Ex.port(p) for p in range(4))
+    e1 = cos_(log_(z ** 2 + 1e-3 * x)) - x + 1e-5 / z
+    e2 = cosh_(w + 1e-3 * y) + y + 1e-4 * w - 2.0
+    e3 = tan_(x + y) / ((x - 2.0) * (x + 3.0) * y ** 2) - 1.0
+    rels = [expr_relation((0, 1, 2, 3), e1, eps=eps), expr_relation((0, 1, 2, 3), e2, eps=eps),
+            expr_relation((0, 1, 2, 3), e3, eps=eps)]
+    # each relation reads only its own variables: ports not used by the
+    # expression are dropped from its variable list below
+    rels = [_used_ports(r) for r in rels]
+    return System(f"butterfly_r{res}", [(lo, hi, res)] * 4, rels, tuple(exposed))
+
+
+def _used_ports(rel: Relation) -> Relation:
+    """The same relation over only the ports its program reads (renumbered)."""
+    ops, consts = rel.expr
+    used = sorted({int(o) >> 8 for o in ops if (int(o) & 0xff) == X_VAR})
+    remap = {p: i for i, p in enumerate(used)}
+    new_ops = np.array([(o & 0xff) + 256 * remap[o >> 8] if (o & 0xff) == X_VAR else o
+                        for o in (int(v) for v in ops)], dtype=np.int32)
+    return Relation(tuple(rel.vars[p] for p in used), 0, rel.coeffs, rel.kind, rel.eps,
+                    (new_ops, consts))
+
+
+def input_exemplar(eps: float = 0.05) -> System:
+    """The input exemplar of Sec. 2.1: u, v, x, y in [-2, 2) at 50 and w, z in
+    [-1, 1) at 80 (ids u0 v1 w2 x3 y4 z5), (v, z) exposed;
+      x^2 + 3|x - y| - 5 = 0,  y^2 v^3 - w^5 <= 0,  cos(u + z x) - w^2 = 0."""
+    x, y = Ex.port(0), Ex.port(1)
+    r1 = expr_relation((3, 4), x ** 2 + 3.0 * abs_(x - y) - 5.0, eps=eps)
+    y2, v2, w2 = Ex.port(0), Ex.port(1), Ex.port(2)
+    r2 = expr_relation((4, 1, 2), y2 ** 2 * v2 ** 3 - w2 ** 5, KIND_LE, eps=eps)
+    u3, z3, x3, w3 = Ex.port(0), Ex.port(1), Ex.port(2), Ex.port(3)
+    r3 = expr_relation((0, 5, 3, 2), cos_(u3 + z3 * x3) - w3 ** 2, eps=eps)
+    axes = [(-2.0, 2.0, 50), (-2.0, 2.0, 50), (-1.0, 1.0, 80), (-2.0, 2.0, 50), (-2.0, 2.0, 50),
+            (-1.0, 1.0, 80)]
+    return System("input_exemplar", axes, [r1, r2, r3], (1, 5))
+
+
+def arrays_3d(res: int = 75, eps: float = 0.05) -> System:
+    """The 3-D arrays example of Sec. 2.4: v, x, z in [-3, 3) and w, y in
+    [-2.5, 2.5) at `res` (ids v0 w1 x2 y3 z4), (w, y) exposed;
+      tan(y + w) + exp(x) - 2 = 0,  x^3 + cos(ln(y^2)) - 1.5 v = 0,
+      w + z + 0.1 v - 0.5 = 0."""
+    y, w, x = Ex.port(0), Ex.port(1), Ex.port(2)
+    r1 = expr_relation((3, 1, 2), tan_(y + w) + exp_(x) - 2.0, eps=eps)
+    x2, y2, v2 = Ex.port(0), Ex.port(1), Ex.port(2)
+    r2 = expr_relation((2, 3, 0), x2 ** 3 + cos_(log_(y2 ** 2)) - 1.5 * v2, eps=eps)
+    w3, z3, v3 = Ex.port(0), Ex.port(1), Ex.port(2)
+    r3 = expr_relation((1, 4, 0), w3 + z3 + 0.1 * v3 - 0.5, eps=eps)
+    axes = [(-3.0, 3.0, res), (-2.5, 2.5, res), (-3.0, 3.0, res), (-2.5, 2.5, res),
+            (-3.0, 3.0, res)]
+    return System(f"arrays3d_r{res}", axes, [r1, r2, r3], (1, 3))
 
 
 def batched_chains(nsys: int = 4096, seed: int = SEED_BASE + 4, res_choices=None,

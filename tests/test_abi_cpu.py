@@ -172,3 +172,37 @@ def test_solve_argument_reuse():
     a6 = pa._network_args(s.axes, s.rels, (0, 2))
     assert pa._network_args(s.axes, s.rels, (0, 2)) is not a6
     assert a6.c_rels[2].coeffs[1] == float(s.rels[2].coeffs[1])
+
+
+def test_expression_relation_checks(lib):
+    """Expression relations (Sec. 2.1, Sec. 2.4): programs are checked on the
+    host before any launch; the library derives tolerances for polynomials only."""
+    from paper_1609_00061_gb300.workloads import Ex, cos_
+    axes = [(-2.0, 2.0, 16), (-2.0, 2.0, 16)]
+    x, y = Ex.port(0), Ex.port(1)
+    good = W.expr_relation((0, 1), cos_(x) - y, eps=0.1)
+    pairs, ops, _ = pa.pa_plan_order(axes, [good], (0,))
+    assert pairs == [] and ops == 0
+    with pytest.raises(pa.PaError) as e:
+        pa.pa_valid_tolerance(good, axes)
+    assert e.value.status == 2
+
+    def prog(ops, consts=(), eps=0.1, arity=2):
+        return W.Relation(tuple(range(arity)), 0, np.zeros(1), 0, eps,
+                          (np.array(ops, np.int32), np.array(consts, np.float64)))
+
+    bad = [prog([W.X_ADD]),                                   # stack underflow
+           prog([W.X_VAR, W.X_VAR]),                          # two values left
+           prog([W.X_VAR + 256 * 5]),                         # port 5 of 2
+           prog([W.X_CONST + 256 * 1], [1.0]),                # constant 1 of 1
+           prog([W.X_VAR, 99]),                               # unknown instruction
+           prog([W.X_VAR, W.X_POWI + 256 * 65]),              # power out of range
+           prog([W.X_VAR], eps=-1.0),                         # no derived tolerance
+           prog([W.X_CONST], [float("nan")]),                 # NaN constant
+           prog([W.X_VAR] * 17 + [W.X_ADD] * 16)]             # 17 stack values
+    for k, r in enumerate(bad):
+        with pytest.raises(pa.PaError) as e:
+            pa.pa_plan_order(axes, [r], (0,))
+        assert e.value.status == 1, k
+    ok = prog([W.X_VAR] * 16 + [W.X_ADD] * 15)                # exactly 16 values
+    pa.pa_plan_order(axes, [ok], (0,))
