@@ -292,6 +292,21 @@ pa_status pa_plot(pa_ctx* ctx, const pa_relation* rel, const pa_axis* axes, int3
 pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t nkeep,
                       const int32_t* keep, pa_array* out, void* stream);
 
+/* One cluster over the counting semiring instead of the Boolean one (the
+ * paper notes that its arrays may take values in any semi-ring, such as the
+ * natural numbers, to count solutions instead of marking them: Sec. 2.2,
+ * footnote on plots): counts(e') = sum over the values of every variable of A
+ * or B not in keep of A(e_A) * B(e_B), the number of latent pixel tuples
+ * behind each output pixel.  `counts` is a device array of uint32, one per
+ * output pixel, row-major over keep (last variable fastest, not bit-packed).
+ * Runs on the tensor cores (0/1 E4M3 products summed in FP32): exact because
+ * every sum is an integer of at most K = the product of the summed
+ * variables' resolutions, which must be <= 2^24.  Supported when every
+ * summed variable belongs to both A and B and B keeps a variable of its own;
+ * other clusters return PA_ERR_UNSUPPORTED. */
+pa_status pa_contract_count(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t nkeep,
+                            const int32_t* keep, uint32_t* counts, void* stream);
+
 /* The whole method (Sec. 3.6): plot every relation, join the plots pairwise in
  * the order chosen by opts->order, and leave the array over `exposed` (in that
  * axis order) in `out`.  nexposed = 0 gives one bit: does the system have a

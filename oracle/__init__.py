@@ -18,6 +18,7 @@ Functions (passages of Spivak et al., arXiv 1609.00061):
   eval_expr, plot_expr  expression relations (Sec. 2.1, Sec. 2.4) and their plot
   gam               Sec. 3.3, Algorithm 1 (all arrays at once; tiny grids)
   contract          Sec. 3.3 Eq. (GAM) on one two-array cluster (Sec. 3.5)
+  contract_count    the same cluster over the counting semiring (Sec. 2.2, footnote)
   reduce            Eq. (GAM) with one array: OR over the dropped variables
   solve             the whole method: plots, then one cluster after another
 """
@@ -82,6 +83,10 @@ def _L():
         lib.or_plot_expr.restype = ctypes.c_int
         lib.or_plot_expr.argtypes = [ctypes.c_int, ctypes.c_int, i32p, f64p, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, f64p, f64p, i32p, u8p]
+        lib.or_contract_count.restype = ctypes.c_int
+        lib.or_contract_count.argtypes = [ctypes.c_int, i32p, u8p, ctypes.c_int, i32p, u8p,
+                                          ctypes.c_int, i32p, i32p,
+                                          ctypes.POINTER(ctypes.c_uint64)]
         lib.or_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -233,6 +238,23 @@ def contract(X: Arr, Y: Arr, keep, vres) -> Arr:
                                len(keep), kvp, vrp, _u8(out))
     assert rc == 0
     return Arr(out, keep)
+
+
+def contract_count(X: Arr, Y: Arr, keep, vres) -> np.ndarray:
+    """One cluster over the counting semiring: the number of values of the
+    summed variables with X and Y both on (uint64 array shaped by keep)."""
+    keep = tuple(int(v) for v in keep)
+    xv, xvp = _i32(X.vars if X.vars else [0])
+    yv, yvp = _i32(Y.vars if Y.vars else [0])
+    kv, kvp = _i32(keep if keep else [0])
+    vr, vrp = _i32(vres)
+    xd = np.array(X.data, dtype=np.uint8, order="C")
+    yd = np.array(Y.data, dtype=np.uint8, order="C")
+    out = np.zeros(tuple(int(vres[v]) for v in keep), dtype=np.uint64)
+    rc = _L().or_contract_count(len(X.vars), xvp, _u8(xd), len(Y.vars), yvp, _u8(yd), len(keep),
+                                kvp, vrp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    assert rc == 0
+    return out
 
 
 def reduce(X: Arr, keep, vres) -> Arr:

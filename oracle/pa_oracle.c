@@ -22,6 +22,8 @@
  *                                        their sample-in-center plot
  *   or_gam                            -- Algorithm 1 (generalized array multiplication)
  *   or_contract_pair                  -- Eq. (GAM) for a two-array cluster (Sec. 3.5)
+ *   or_contract_count                 -- the same cluster over the counting semiring
+ *                                        (Sec. 2.2, footnote on plots)
  *
  * Parity status: every function here is pinned by the tests under tests/
  * (brute force, closed forms, the Appendix A example, no-false-negative points).
@@ -455,6 +457,70 @@ int or_contract_pair(int nx, const int* xvars, const uint8_t* X, int ny, const i
       }
     }
     out[o] = acc;
+  }
+  return 0;
+}
+
+/* The same cluster over the counting semiring (Sec. 2.2, footnote on plots:
+ * arrays with values in the natural numbers count solutions): out(e') is the
+ * sum over every value of the variables not kept of X(e_X) * Y(e_Y), each
+ * product 0 or 1.  A plain loop over the kept entries and, inside, over every
+ * value of the summed variables. */
+int or_contract_count(int nx, const int* xvars, const uint8_t* X, int ny, const int* yvars,
+                      const uint8_t* Y, int nkeep, const int* keep, const int* vres,
+                      uint64_t* out) {
+  int vlist[3 * OR_MAX_DIM], nv = 0;
+  for (int k = 0; k < nkeep; ++k) vlist[nv++] = keep[k];
+  for (int s = 0; s < nx + ny; ++s) {
+    int v = (s < nx) ? xvars[s] : yvars[s - nx];
+    int seen = 0;
+    for (int k = 0; k < nv; ++k) seen |= (vlist[k] == v);
+    if (!seen) vlist[nv++] = v;
+  }
+  int64_t xs[3 * OR_MAX_DIM], ys[3 * OR_MAX_DIM], r[3 * OR_MAX_DIM];
+  for (int k = 0; k < nv; ++k) {
+    xs[k] = 0;
+    ys[k] = 0;
+    r[k] = vres[vlist[k]];
+  }
+  int64_t st = 1;
+  for (int j = nx - 1; j >= 0; --j) {
+    for (int k = 0; k < nv; ++k)
+      if (vlist[k] == xvars[j]) xs[k] += st;
+    st *= vres[xvars[j]];
+  }
+  st = 1;
+  for (int j = ny - 1; j >= 0; --j) {
+    for (int k = 0; k < nv; ++k)
+      if (vlist[k] == yvars[j]) ys[k] += st;
+    st *= vres[yvars[j]];
+  }
+  int64_t out_size = 1;
+  for (int k = 0; k < nkeep; ++k) out_size *= r[k];
+  int64_t sum_size = 1;
+  for (int k = nkeep; k < nv; ++k) sum_size *= r[k];
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t o = 0; o < out_size; ++o) {
+    int64_t rest = o, base_x = 0, base_y = 0;
+    for (int k = nkeep - 1; k >= 0; --k) {
+      int64_t v = rest % r[k];
+      rest /= r[k];
+      base_x += xs[k] * v;
+      base_y += ys[k] * v;
+    }
+    uint64_t total = 0;
+    for (int64_t s = 0; s < sum_size; ++s) {
+      /* decode s into the summed variables' values, last one fastest */
+      int64_t rs = s, xi = base_x, yi = base_y;
+      for (int k = nv - 1; k >= nkeep; --k) {
+        int64_t v = rs % r[k];
+        rs /= r[k];
+        xi += xs[k] * v;
+        yi += ys[k] * v;
+      }
+      total += (uint64_t)X[xi] * (uint64_t)Y[yi];
+    }
+    out[o] = total;
   }
   return 0;
 }

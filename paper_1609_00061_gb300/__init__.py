@@ -177,6 +177,15 @@ def pa_contract(ctx, A: BitArray, B: BitArray, keep, out: BitArray, stream=None)
     return out
 
 
+def pa_contract_count(ctx, A: BitArray, B: BitArray, keep, counts, stream=None):
+    """Counting-semiring cluster: `counts` is a CUDA int32 tensor of
+    prod(res of keep) elements receiving the uint32 counts, row-major over keep."""
+    a, b = A.c(), B.c()
+    _check(_lib().pa_contract_count(ctx, ctypes.byref(a), ctypes.byref(b), len(keep), _i32(keep),
+                                    ctypes.c_void_p(counts.data_ptr()), _stream_ptr(stream)), ctx)
+    return counts
+
+
 class _NetArgs:
     """The marshalled arguments of the last pa_solve_network call, reused while
     the same Python objects hold the same values.  Coefficients are not copied:
@@ -461,6 +470,20 @@ class Engine:
             res[v] = r
         out = BitArray.empty(keep, [res[v] for v in keep], self.device)
         return pa_contract(self.ctx, A, B, keep, out, stream)
+
+    def contract_count(self, A: BitArray, B: BitArray, keep, stream=None):
+        """Counts over the counting semiring (int32 tensor shaped by keep's resolutions)."""
+        import torch
+        res = {}
+        for v, r in zip(A.vars + B.vars, A.res + B.res):
+            res[v] = r
+        shape = [res[v] for v in keep]
+        n = 1
+        for r in shape:
+            n *= r
+        out = torch.empty(n, dtype=torch.int32, device=f"cuda:{self.device}")
+        pa_contract_count(self.ctx, A, B, keep, out, stream)
+        return out.view(*shape)
 
     def solve(self, system, order="greedy", pairs=None, strict=False, stream=None, out=None,
               model=None):

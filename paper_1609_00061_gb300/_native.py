@@ -133,7 +133,8 @@ class PaSystem(ctypes.Structure):
 
 EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_words",
            "pa_profile_enable", "pa_profile_read",
-           "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_solve_network", "pa_solve_batch",
+           "pa_valid_tolerance", "pa_plot", "pa_contract", "pa_contract_count",
+           "pa_solve_network", "pa_solve_batch",
            "pa_batch_create", "pa_batch_run", "pa_batch_stats", "pa_batch_destroy",
            "pa_solve_network_static", "pa_plan_order", "pa_tree_cost",
            "pa_mlp_create", "pa_mlp_destroy", "pa_mlp_num_params", "pa_mlp_get_params",
@@ -176,6 +177,8 @@ def load(build_if_missing: bool = True):
     lib.pa_plot.restype = c_i32
     lib.pa_contract.argtypes = [vp, P(PaArray), P(PaArray), c_i32, P(c_i32), P(PaArray), vp]
     lib.pa_contract.restype = c_i32
+    lib.pa_contract_count.argtypes = [vp, P(PaArray), P(PaArray), c_i32, P(c_i32), vp, vp]
+    lib.pa_contract_count.restype = c_i32
     lib.pa_solve_network.argtypes = [vp, c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32),
                                      P(PaOptions), P(PaArray), P(PaStats), vp]
     lib.pa_solve_network.restype = c_i32

@@ -87,7 +87,7 @@ bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end()
 
 // ------------------------------------------------------------ program
 enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
-              OP_MMA, OP_CENTRES, OP_PLOT_EXPR };
+              OP_MMA, OP_CENTRES, OP_PLOT_EXPR, OP_PERMUTE };
 
 struct Op {
   OpKind kind;
@@ -110,6 +110,7 @@ const char* op_name(const Op& op) {
     case OP_PLOT: return "plot_kernel";
     case OP_CENTRES: return "plot_centres_kernel";
     case OP_PLOT_EXPR: return "plot_expr_kernel";
+    case OP_PERMUTE: return "permute_u32_kernel";
     case OP_MEMSET: return "memset";
     case OP_RESHAPE:
       return op.rd.mode == kReshapeTranspose ? "reshape_transpose_kernel"
@@ -722,6 +723,82 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
   return C;
 }
 
+// One cluster over the counting semiring (the paper's footnote on other
+// semi-rings, Sec. 2.2): out(e') = sum over the summed variables of
+// A(e_A) * B(e_B), the number of latent pixel tuples behind each output
+// pixel.  On the tensor cores with the > 0 threshold left out: the operands
+// are 0/1, so every sum is an integer <= K, exact in FP32 up to 2^24.
+// Supported when every summed variable is shared by A and B (no axis private
+// to one operand) and both keep a variable of their own or a shared one.
+void join_count(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
+                const std::vector<int64_t>& vres, uint32_t* out) {
+  const JoinShape js = analyze_join(X, Y, keep, vres);
+  if (js.hadamard || js.outer || js.dot)
+    bd.fail(PA_ERR_UNSUPPORTED, "counting: A and B must share a summed variable and B must keep "
+                                "a variable A does not have");
+  if (js.private_a != 1.0 || js.private_b != 1.0)
+    bd.fail(PA_ERR_UNSUPPORTED, "counting: every summed variable must be shared by A and B");
+  if (js.K > (1 << 24)) bd.fail(PA_ERR_UNSUPPORTED, "counting: more than 2^24 summed values");
+  if (tensor_map_encoder() == nullptr) bd.fail(PA_ERR_UNSUPPORTED, "counting needs the tensor maps");
+  const double M = (double)js.M, N = js.nbits, nb = (double)js.nbatch;
+  if (nb * M >= 2147483647.0 || N >= 2147483647.0 ||
+      nb * (M + N) * (ceil((double)js.K / 128) * 128) > 4e9)
+    bd.fail(PA_ERR_TOO_LARGE, "counting: operands too large for the tensor-core expansion");
+  bd.st.pixel_ops_dense += js.cost;
+  bd.st.n_joins++;
+  const BitArr& A = js.swap ? Y : X;
+  const BitArr& B = js.swap ? X : Y;
+  BitArr Am = conform(bd, A, make_arr(js.a_axes, vres, js.kinner));
+  BitArr Bm = conform(bd, B, make_arr(js.b_axes, vres, js.ninner));
+  // the sums come out row-major over c_axes (batch, M, N); keep may order them
+  // otherwise
+  const bool natural = (js.c_axes == keep);
+  const int64_t total = (int64_t)(nb * M * N);
+  uint32_t* sums = natural ? out : static_cast<uint32_t*>(bd.alloc((size_t)total * 4));
+  MmaDesc md;
+  memset(&md, 0, sizeof md);
+  md.A = Am.w;
+  md.B = Bm.w;
+  md.C = nullptr;
+  md.counts = sums;
+  md.M = js.M;
+  md.N = (int64_t)js.nbits;
+  md.K = js.K;
+  md.a_row_words = Am.row_words();
+  md.nbatch = js.nbatch;
+  md.err = bd.d_err;
+  mma_plan(md);
+  md.Ab = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.M * md.Kp)));
+  md.Bb = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.N * md.Kp)));
+  bd.pend_mma.push_back(md);
+  bd.st.mma_macs += nb * M * N * (double)js.K;
+  bd.st.n_mma++;
+  flush_mma(bd);
+  if (!natural) {
+    const int nd = (int)keep.size();
+    std::vector<int64_t> ext(nd), stride(nd);
+    for (int a = 0; a < nd; ++a) {
+      ext[a] = vres[keep[a]];
+      int64_t st = 1;
+      bool after = false;
+      for (int v : js.c_axes) {
+        if (after) st *= vres[v];
+        if (v == keep[a]) after = true;
+      }
+      stride[a] = st;
+    }
+    Op op;
+    op.kind = OP_PERMUTE;
+    op.a = reinterpret_cast<const uint64_t*>(sums);
+    op.p = reinterpret_cast<uint64_t*>(out);
+    op.n = nd;
+    op.off0 = bd.put(ext.data(), ext.size(), 16);
+    op.off1 = bd.put(stride.data(), stride.size(), 16);
+    op.count = total;
+    bd.ops.push_back(op);
+  }
+}
+
 // ------------------------------------------------------------ validation
 void check_axes(pa_ctx* ctx, int32_t nvars, const pa_axis* axes) {
   PA_CHECK_ARG(nvars >= 0 && (nvars == 0 || axes), "axes: null pointer or negative nvars");
@@ -1226,6 +1303,11 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
         launch_plot(reinterpret_cast<const PlotJob*>(blob + op.off0), op.n, op.count, op.i0,
                     op.i1, op.i2, op.i3, op.m, reinterpret_cast<const ZeroRange*>(blob + op.off1),
                     (int)op.nw, op.zw, s);
+        break;
+      case OP_PERMUTE:
+        launch_permute_u32(reinterpret_cast<const uint32_t*>(op.a), reinterpret_cast<uint32_t*>(op.p),
+                           op.n, reinterpret_cast<const int64_t*>(blob + op.off0),
+                           reinterpret_cast<const int64_t*>(blob + op.off1), op.count, s);
         break;
       case OP_PLOT_EXPR:
         launch_plot_expr(reinterpret_cast<const ExprJob*>(blob + op.off0), op.n, op.count, s);
@@ -2245,6 +2327,42 @@ pa_status pa_contract(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t
     flush_rowor(bd);
     if (r.w != target.w) reshape(bd, r, target);
   });
+}
+
+pa_status pa_contract_count(pa_ctx* ctx, const pa_array* A, const pa_array* B, int32_t nkeep,
+                            const int32_t* keep, uint32_t* counts, void* stream) {
+  if (!ctx) return PA_ERR_INVALID_ARG;
+  std::vector<int> kv;
+  std::vector<int64_t> vres;
+  try {
+    check_array(ctx, A, "A");
+    check_array(ctx, B, "B");
+    PA_CHECK_ARG(counts != nullptr, "counts: null pointer");
+    PA_CHECK_ARG(nkeep >= 1 && nkeep <= PA_MAX_DIM && keep, "keep: 1..8 variables");
+    int maxv = 0;
+    for (int i = 0; i < A->ndim; ++i) maxv = std::max(maxv, A->vars[i]);
+    for (int i = 0; i < B->ndim; ++i) maxv = std::max(maxv, B->vars[i]);
+    for (int i = 0; i < A->ndim; ++i) PA_CHECK_ARG(A->vars[i] >= 0, "A: negative variable id");
+    for (int i = 0; i < B->ndim; ++i) PA_CHECK_ARG(B->vars[i] >= 0, "B: negative variable id");
+    vres.assign(maxv + 1, 0);
+    for (int i = 0; i < A->ndim; ++i) vres[A->vars[i]] = A->res[i];
+    for (int i = 0; i < B->ndim; ++i) {
+      const int v = B->vars[i];
+      PA_CHECK_ARG(vres[v] == 0 || vres[v] == B->res[i], "A and B disagree on a resolution");
+      vres[v] = B->res[i];
+    }
+    for (int i = 0; i < nkeep; ++i) {
+      const int v = keep[i];
+      PA_CHECK_ARG(v >= 0 && v <= maxv && vres[v] > 0, "keep: variable not in A or B");
+      for (int j = 0; j < i; ++j) PA_CHECK_ARG(keep[j] != v, "keep: repeated variable");
+      kv.push_back(v);
+    }
+  } catch (const Fail& f) {
+    return f.st;
+  }
+  BitArr a = from_pa(*A), b = from_pa(*B);
+  return run_call(ctx, static_cast<cudaStream_t>(stream), nullptr,
+                  [&](Builder& bd) { join_count(bd, a, b, kv, vres, counts); });
 }
 
 pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,

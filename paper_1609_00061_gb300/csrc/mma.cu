@@ -330,6 +330,17 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
       tmem_ld32(ta, v);
       tmem_ld32(ta + 32u, v + 32);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (d.counts) {
+        // counting semiring: every sum is an integer <= K <= 2^24, exact in FP32
+        const int64_t n0 = nt * BN + c * 64;
+        if (ok && !*sfail && m < d.M) {
+          uint32_t* row = d.counts + (b * d.M + m) * d.N;
+#pragma unroll
+          for (int j = 0; j < 64; ++j)
+            if (n0 + j < d.N) row[n0 + j] = (uint32_t)__uint_as_float(v[j]);
+        }
+        continue;
+      }
       uint64_t word = 0;
 #pragma unroll
       for (int j = 0; j < 64; ++j) word |= (uint64_t)(__uint_as_float(v[j]) > 0.0f) << j;
@@ -374,7 +385,32 @@ __global__ void random_bits_kernel(uint64_t* __restrict__ w, int64_t nwords, int
   }
 }
 
+// ext and stride are device arrays of ndim entries (in the call's blob)
+__global__ void permute_u32_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                   int ndim, const int64_t* __restrict__ ext,
+                                   const int64_t* __restrict__ stride, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rest = i, src = 0;
+    for (int a = ndim - 1; a >= 0; --a) {
+      const int64_t e = __ldg(ext + a);
+      const int64_t q = rest % e;
+      rest /= e;
+      src += q * __ldg(stride + a);
+    }
+    out[i] = in[src];
+  }
+}
+
 }  // namespace
+
+void launch_permute_u32(const uint32_t* in, uint32_t* out, int ndim, const int64_t* d_ext,
+                        const int64_t* d_stride, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  permute_u32_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, ndim, d_ext, d_stride, total);
+}
 
 void launch_random_bits(uint64_t* w, int64_t nwords, int64_t row_words, int64_t valid,
                         double density, uint64_t seed, cudaStream_t s) {

@@ -221,6 +221,8 @@ struct MmaDesc {
   int64_t m_tiles, n_tiles;
   int32_t BN;                 // columns per tile: 64, 128 or 256
   int* err;                   // device error word: set when a bounded wait runs out
+  uint32_t* counts;           // when not null: the sums themselves, [nbatch][M][N]
+                              // (counting semiring), and C is not written
 };
 void mma_plan(MmaDesc& d);    // BN, Nw, Kp and the tile counts from M, N, K, nbatch
 int64_t mma_ctas(const MmaDesc& d);
@@ -237,6 +239,12 @@ void launch_unpack(const MmaDesc* d_descs, int nprob, int64_t blocks_a, int64_t 
 // and CTA offsets (nprob + 1 entries) on the device.
 cudaError_t launch_mma(const MmaDesc* d_descs, const CUtensorMap* d_maps, const int64_t* d_cta0,
                        int nprob, int64_t grid, cudaStream_t s);
+// out[i] = in[src(i)] for a row-major array whose axes are a permutation of
+// the input's: out axis a has extent d_ext[a] and steps d_stride[a] elements
+// of the input (one thread per output element; d_ext and d_stride are DEVICE
+// arrays of ndim entries).
+void launch_permute_u32(const uint32_t* in, uint32_t* out, int ndim, const int64_t* d_ext,
+                        const int64_t* d_stride, int64_t total, cudaStream_t s);
 // Random bit rows of the given density (autotuning inputs); padding stays zero.
 void launch_random_bits(uint64_t* w, int64_t nwords, int64_t row_words, int64_t valid,
                         double density, uint64_t seed, cudaStream_t s);

@@ -129,3 +129,39 @@ def test_solve_with_expressions_matches_brute_force(orc):
     want = orc.gam(link_res, [p.data for p in plots], [p.vars for p in plots], small.exposed)
     got = orc.solve(small.axes, small.rels, small.exposed).data
     assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------- counting semiring
+@pytest.mark.parametrize("case", [((0, 1), (1, 2), (0, 2), {0: 5, 1: 7, 2: 3}),
+                                  ((0, 1, 2), (2, 1, 3), (0, 3), {0: 4, 1: 3, 2: 5, 3: 6}),
+                                  ((0, 1, 2), (0, 2, 3), (3, 0, 1), {0: 2, 1: 4, 2: 6, 3: 3}),
+                                  ((0, 1), (1, 2), (2,), {0: 4, 1: 5, 2: 3}),
+                                  ((1, 0), (1, 0), (), {0: 6, 1: 7})])
+def test_oracle_count_against_einsum(orc, case):
+    """The counting cluster (Sec. 2.2 footnote) against numpy's integer einsum,
+    and its support against the Boolean cluster."""
+    xv, yv, keep, rmap = case
+    rng = np.random.default_rng(len(xv) * 10 + len(keep))
+    vres = [rmap[v] for v in range(max(rmap) + 1)]
+    X = (rng.random([rmap[v] for v in xv]) < 0.5).astype(np.uint8)
+    Y = (rng.random([rmap[v] for v in yv]) < 0.5).astype(np.uint8)
+    letters = "abcdefgh"
+    spec = (''.join(letters[v] for v in xv) + "," + ''.join(letters[v] for v in yv) + "->"
+            + ''.join(letters[v] for v in keep))
+    want = np.einsum(spec, X.astype(np.int64), Y.astype(np.int64))
+    got = orc.contract_count(orc.Arr(X, xv), orc.Arr(Y, yv), keep, vres)
+    assert np.array_equal(got.astype(np.int64), want)
+    boolean = orc.contract(orc.Arr(X, xv), orc.Arr(Y, yv), keep, vres).data
+    assert np.array_equal(boolean, (want > 0).astype(np.uint8))
+
+
+def test_oracle_count_circle_parabola(orc):
+    """x^2 + y^2 = 1 and y = z^2 - 1/2: for (x, z) pixels near a solution the
+    number of y pixels shared by both plots is small and positive; everywhere
+    the count is zero exactly where the Boolean product is off."""
+    sy = W.circle_parabola(res=64)
+    a, b = (orc.plot_relation(r, sy.axes) for r in sy.rels)
+    cnt = orc.contract_count(a, b, (0, 2), [64, 64, 64])
+    boolean = orc.solve(sy.axes, sy.rels, sy.exposed).data
+    assert np.array_equal(cnt > 0, boolean > 0)
+    assert 0 < cnt.max() <= 64
