@@ -147,58 +147,103 @@ def sample_ops(s):
 
 
 def cpu_baseline():
+    """The oracle as it stands on the host cores: the chain sample on every core
+    (the headline figure) and on one core, and the circle-parabola (256) and
+    ternary (256^3 arrays) workloads in full on every core."""
     import oracle
     from paper_1609_00061_gb300 import workloads as W
     oracle.build()
+    cores = oracle.num_threads()
     s = reference_sample(W)
-    oracle.solve(s.axes, s.rels, s.exposed)
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        oracle.solve(s.axes, s.rels, s.exposed)
-        n += 1
-        if time.perf_counter() - t0 > 10.0 or n >= 20:
-            break
-    dt = (time.perf_counter() - t0) / n
-    return {"value": sample_ops(s) / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": s.meta["sample"] + f", {n} repetitions"}
+
+    def timed(sy, max_s, max_n):
+        oracle.solve(sy.axes, sy.rels, sy.exposed)
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            oracle.solve(sy.axes, sy.rels, sy.exposed)
+            n += 1
+            if time.perf_counter() - t0 > max_s or n >= max_n:
+                break
+        return (time.perf_counter() - t0) / n, n
+
+    dt, n = timed(s, 10.0, 20)
+    out = {"value": sample_ops(s) / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": s.meta["sample"] + f", {n} repetitions"}
+    oracle.set_num_threads(1)
+    try:
+        dt1, n1 = timed(s, 3.0, 2)
+    finally:
+        oracle.set_num_threads(cores)
+    out["single_core"] = {"value": sample_ops(s) / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                          "repetitions": n1}
+    other = {}
+    for sy in (W.circle_parabola(res=256), W.ternary(res=256)):
+        d, k = timed(sy, 5.0, 3)
+        other[sy.name] = {"ms_per_solve": d * 1e3, "cores": cores, "repetitions": k,
+                          "pixel_ops_per_solve": solve_ops(sy)}
+    out["other_workloads"] = other
+    return out
+
+
+def solve_ops(sy):
+    """Naive cost sum r^Lambda of the library's greedy plan (host planning only)."""
+    import paper_1609_00061_gb300 as pa
+    return pa.pa_plan_order(sy.axes, sy.rels, sy.exposed)[1]
 
 
 # ------------------------------------------------------------------ our arm
-SMEM_GBS = 152 * 32 * 4 * 2070e6 / 1e9   # 152 SMs x 32 banks x 4 B x 2070 MHz
-FP32_TFLOPS = 2.0 * 152 * 128 * 2070e6 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
-
-
 def fp8_tflops():
     return 2.0 * (load_peaks().get("bf16_tflops") or 1900.0)
 
 
-def kernel_rooflines(kernels, stats_step, steps, sysm):
-    """Roofline of every kernel with a defined algorithmic work, largest share first."""
-    out = []
+def kernel_rooflines(kernels, stats_step, steps, sysm, pk):
+    """Roofline of every kernel with a defined algorithmic work, largest share
+    first; pk: the pipe peaks pa_measure_peaks measured on this GPU.  The
+    contraction gets three lines: the 32-bit logic pipe on the OR work it
+    executed (the bit path's roofline), the shared-memory load bandwidth on
+    the table words it read, and HBM on its operand bytes."""
+    out, extra = [], []
     total = sum(v[1] for k, v in kernels.items() if k != "words_or") or 1.0
     words = kernels.get("words_or", (0, 0.0))[0]
     for name, (launches, ms) in kernels.items():
         if name == "words_or" or launches == 0 or ms <= 0:
             continue
         t = ms / 1e3 / launches
+        share = ms / total
         if name == "rowor_kernel":
+            wl = words / launches
+            # every executed table word is one 64-bit OR: two 32-bit LOP3
+            ops = 2.0 * wl
+            ach = ops / t / 1e9
+            peak = pk["lop3_ops_per_s"] / 1e9
+            out.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
+                        "unit": "Gop/s", "frac": ach / peak, "traffic": None,
+                        "limit": f"32-bit LOP3 pipe, measured by pa_measure_peaks "
+                                 f"({pk['lop3_per_clk_sm']:.1f} per SM per clock at "
+                                 f"{pk['sm_clock_hz'] / 1e6:.0f} MHz)",
+                        "work_per_launch": f"{wl:.4g} 64-bit table words OR-ed (2 LOP3 each), "
+                                           f"counted by the kernel",
+                        "share": share})
+            b = 8.0 * wl
+            extra.append({"kernel": name, "bound": "smem", "achieved": b / t / 1e9,
+                          "peak": pk["smem_bytes_per_s"] / 1e9, "unit": "GB/s",
+                          "frac": (b / t) / pk["smem_bytes_per_s"],
+                          "limit": "shared-memory loads, measured by pa_measure_peaks",
+                          "work_per_launch": f"{b:.4g} bytes of table words read",
+                          "share": share})
             # algorithmic bytes of a Boolean r x r x r product: the bit-packed A
-            # and B read once and C written once, 3 r^2 / 8 bytes; the joins the
-            # row-OR path ran (all but the tensor-core ones) over its launches
+            # and B read once and C written once, 3 r^2 / 8 bytes
             r = sysm.axes[0][2]
             joins = (stats_step["n_joins"] - stats_step.get("n_mma", 0)) * steps
-            b = 3.0 * r * r / 8.0 * joins / launches
-            ach = b / t / 1e9
-            peak = load_peaks().get("hbm_gbs") or 6800.0
-            out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak,
-                        "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                        "limit": "HBM copy bandwidth, MEASURED_PEAKS.json (operands L2-resident "
-                                 "between launches)",
-                        "work_per_launch": f"{b:.4g} bytes: A, B read and C written once, "
-                                           f"{joins / launches:.3g} joins of {r}^3",
-                        "executed_words_or": f"{words / launches:.4g} tile words OR-ed per launch",
-                        "share": ms / total})
+            hb = 3.0 * r * r / 8.0 * joins / launches
+            hpk = load_peaks().get("hbm_gbs") or 6800.0
+            extra.append({"kernel": name, "bound": "hbm", "achieved": hb / t / 1e9, "peak": hpk,
+                          "unit": "GB/s", "frac": hb / t / 1e9 / hpk,
+                          "limit": "HBM copy bandwidth, MEASURED_PEAKS.json",
+                          "work_per_launch": f"{hb:.4g} bytes: A, B read and C written once, "
+                                            f"{joins / launches:.3g} joins of {r}^3",
+                          "share": share})
         elif name == "mma_bool_kernel":
             # 2 flops per multiply-add of the unpadded clusters (M x N x K each)
             macs = stats_step.get("mma_macs", 0.0) * steps / launches
@@ -209,19 +254,20 @@ def kernel_rooflines(kernels, stats_step, steps, sysm):
                         "limit": "dense FP8 tensor rate: measured bf16 burst x 2 (nominal "
                                  "FP8/BF16 ratio), MEASURED_PEAKS.json",
                         "work_per_launch": f"{macs:.4g} multiply-adds",
-                        "share": ms / total})
+                        "share": share})
         elif name == "plot_kernel":
             # algorithmic work per pixel: the row polynomial sum_j g_j y^j, D FMAs
             D = max(r.degree for r in sysm.rels)
             pix = stats_step["pixels_plotted"] * steps / launches
             ach = 2.0 * D * pix / t / 1e12
-            out.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_TFLOPS,
-                        "unit": "TFLOP/s", "frac": ach / FP32_TFLOPS, "traffic": None,
-                        "limit": "FP32 FMA lanes, 152 SMs x 128 x 2 flops x 2070 MHz, derived",
+            peak = pk["fp32_flops_per_s"] / 1e12
+            out.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
+                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                        "limit": "FP32 FMA, measured by pa_measure_peaks",
                         "work_per_launch": f"{pix:.4g} pixels x {2 * D} flops",
-                        "share": ms / total})
+                        "share": share})
     out.sort(key=lambda r: -r["share"])
-    return out
+    return out, extra
 
 
 def run_batched(eng, pa, W, dev, reps=5):
@@ -370,6 +416,64 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
                       "first replay"}
 
 
+def run_other(eng, pa, W, pk, reps=50):
+    """The other workloads through the same calls: the circle-parabola system
+    (256) and the ternary network (256^3 arrays) solved whole; the butterfly
+    of Sec. 2.4 (expression relations) at the paper's printed size and at 2048
+    pixels per axis; and one counting-semiring cluster of two 2048^2 chain
+    plots on the tensor cores.  CUDA events on the launching stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+
+    def time_calls(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    for sy in (W.circle_parabola(res=256), W.ternary(res=256), W.butterfly(res=125),
+               W.butterfly(res=2048)):
+        o = pa.BitArray.empty(sy.exposed, [sy.axes[v][2] for v in sy.exposed], eng.device)
+        st = {}
+
+        def solve(sy=sy, o=o):
+            st.update(pa.pa_solve_network(eng.ctx, sy.axes, sy.rels, sy.exposed, o))
+        ms = time_calls(solve, reps)
+        rec = {"ms_per_solve": ms, "pixel_ops_dense": st["pixel_ops_dense"],
+               "gpixel_ops_per_s": st["pixel_ops_dense"] / (ms / 1e3) / 1e9,
+               "pixels_plotted": st["pixels_plotted"], "launches": st["n_launches"]}
+        if sy.name.startswith("butterfly"):
+            pa.pa_profile_enable(eng.ctx, True)
+            for _ in range(5):
+                solve()
+            kern = pa.pa_profile_read(eng.ctx)
+            pa.pa_profile_enable(eng.ctx, False)
+            n, kms = kern.get("plot_expr_kernel", (0, 0.0))
+            if n:
+                rec["plot_expr_gpixels_per_s"] = st["pixels_plotted"] / (kms / n / 1e3) / 1e9
+        out[sy.name] = rec
+    # one counting cluster: two plots of the chain workload at 2048
+    ch = W.chain(res=2048, nrel=2)
+    a = eng.plot(ch.rels[0], ch.axes)
+    b = eng.plot(ch.rels[1], ch.axes)
+    cnt = torch.empty(2048 * 2048, dtype=torch.int32, device=f"cuda:{eng.device}")
+    ms = time_calls(lambda: pa.pa_contract_count(eng.ctx, a, b, (0, 2), cnt), reps)
+    tf = 2.0 * 2048 ** 3 / (ms / 1e3) / 1e12
+    out["count_2048cube"] = {"ms": ms, "tflops": tf, "peak_tflops": fp8_tflops(),
+                             "frac": tf / fp8_tflops(),
+                             "what": "pa_contract_count of two 2048^2 chain plots (counting "
+                                     "semiring, tensor cores): 2 M N K flops per call, the "
+                                     "operand expansion and the permute-free epilogue included"}
+    return out
+
+
 def rank_system(W, rank):
     """The chain instance rank `rank` solves: same shape on every rank, its own
     coefficients (seed + rank), so per-rank work is fixed as ranks are added."""
@@ -401,6 +505,8 @@ def run_ours(args, rank, world, local_rank):
     # path choice then weighs each cluster with those rates
     rates = eng.autotune()
     eng.set_path(args.path)
+    # the pipes' peaks on this GPU: the denominators of the kernels' rooflines
+    peaks_live = pa.pa_measure_peaks(eng.ctx)
     sysm = rank_system(W, rank)
     # one logged solve measures the densities of this system's intermediates,
     # which the automatic path choice then prefers to its independence estimate
@@ -472,7 +578,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         eng.close()
         return
-    rl = kernel_rooflines(kernels, st, args.steps, sysm)
+    rl, rl_extra = kernel_rooflines(kernels, st, args.steps, sysm, peaks_live)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -485,11 +591,11 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(out.words.numel() * 8)},
         "gpu_launches": int(st["n_launches"]) * args.steps,
-        "peaks": {"hbm_gbs": load_peaks().get("hbm_gbs"), "smem_gbs_derived": SMEM_GBS,
-                  "fp32_tflops_derived": FP32_TFLOPS, "fp8_tflops_derived": fp8_tflops()},
+        "peaks": {"hbm_gbs": load_peaks().get("hbm_gbs"), "fp8_tflops_derived": fp8_tflops()},
         "clocks": clk,
         "roofline": (rl[0] if rl else None),
-        "roofline_other": rl[1:],
+        "roofline_other": rl[1:] + rl_extra,
+        "measured_peaks": peaks_live,
         "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items()
                     if k != "words_or"},
         "kernel_timing": "per-launch CUDA events on the launching stream, over a second pass "
@@ -500,6 +606,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batched:
         line["batched"] = run_batched(eng, pa, W, dev)
         line["learned"] = run_learned(eng, pa, W)
+        line["other_workloads"] = run_other(eng, pa, W, peaks_live)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

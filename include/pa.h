@@ -264,6 +264,32 @@ pa_status pa_autotune(pa_ctx* ctx, pa_rates* out, void* stream);
 pa_status pa_get_rates(const pa_ctx* ctx, pa_rates* out);
 pa_status pa_set_rates(pa_ctx* ctx, const pa_rates* rates);
 
+/* Check of the failure path of the bounded device waits: enqueues one kernel
+ * whose mbarrier wait can never complete and gives up after limit_ns
+ * (1e3 .. 2e9), exactly as the contraction kernels' waits do, leaving the
+ * context's error word set.  The next pa_sync on that stream returns
+ * PA_ERR_TIMEOUT, clears the word, and the context stays usable. */
+pa_status pa_wait_selftest(pa_ctx* ctx, int64_t limit_ns, void* stream);
+
+/* Measured throughput of the pipes this library's kernels run on (the
+ * denominators of their rooflines), on the context's GPU: long chains of
+ * independent operations in 1024 threads on every SM, timed with CUDA events
+ * after a warm-up launch on `stream`, with each block's SM cycle counter.
+ * Blocks the host; allocates and frees a few KB of device memory. */
+typedef struct {
+  int32_t sms;                  /* streaming multiprocessors used */
+  double sm_clock_hz;           /* SM clock during the LOP3 probe */
+  double lop3_ops_per_s;        /* 32-bit three-input logic operations (lop3.b32) */
+  double lop3_per_clk_sm;
+  double smem_bytes_per_s;      /* shared-memory load bandwidth, 8-byte loads */
+  double smem_bytes_per_clk_sm;
+  double fp32_flops_per_s;      /* FP32 fused multiply-add, 2 flops each */
+  double fp32_flops_per_clk_sm;
+  double fp64_flops_per_s;      /* FP64 multiply and add, not fused */
+  double fp64_flops_per_clk_sm;
+} pa_peaks;
+pa_status pa_measure_peaks(pa_ctx* ctx, pa_peaks* out, void* stream);
+
 /* Number of uint64 words of a pa_array of this shape (host only, no GPU). */
 int64_t pa_array_words(int32_t ndim, const int32_t* res);
 

@@ -88,6 +88,8 @@ def _L():
                                           ctypes.c_int, i32p, i32p,
                                           ctypes.POINTER(ctypes.c_uint64)]
         lib.or_num_threads.restype = ctypes.c_int
+        lib.or_set_num_threads.restype = None
+        lib.or_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -108,6 +110,11 @@ def _u8(a):
 
 def num_threads() -> int:
     return int(_L().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads the oracle's loops use from now on."""
+    _L().or_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------- polynomials

@@ -532,3 +532,13 @@ int or_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads the loops above may use from now on (timing the oracle on one core
+ * and on all of them). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

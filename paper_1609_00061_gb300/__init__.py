@@ -420,6 +420,19 @@ def pa_autotune(ctx, stream=None) -> dict:
     return r.as_dict()
 
 
+def pa_wait_selftest(ctx, limit_ns=1_000_000, stream=None):
+    """Enqueue a bounded device wait that runs out (the next pa_sync reports it)."""
+    _check(_lib().pa_wait_selftest(ctx, int(limit_ns), _stream_ptr(stream)), ctx)
+
+
+def pa_measure_peaks(ctx, stream=None) -> dict:
+    """Measured LOP3, shared-memory, FP32 and FP64 throughput of this GPU."""
+    from ._native import PaPeaks
+    p = PaPeaks()
+    _check(_lib().pa_measure_peaks(ctx, ctypes.byref(p), _stream_ptr(stream)), ctx)
+    return p.as_dict()
+
+
 def pa_get_rates(ctx) -> dict:
     r = PaRates()
     _check(_lib().pa_get_rates(ctx, ctypes.byref(r)), ctx)

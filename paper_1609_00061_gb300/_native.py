@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
 _ROOT = os.path.dirname(_HERE)
 INCLUDE = os.path.join(_ROOT, "include")
 
-CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu", "mma.cu", "expr.cu"]
+CU_SOURCES = ["api.cu", "plot.cu", "contract.cu", "mlp.cu", "mma.cu", "expr.cu", "probe.cu"]
 CPP_SOURCES = ["planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -125,6 +125,17 @@ class PaRates(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PaPeaks(ctypes.Structure):
+    _fields_ = [("sms", c_i32), ("sm_clock_hz", c_f64), ("lop3_ops_per_s", c_f64),
+                ("lop3_per_clk_sm", c_f64), ("smem_bytes_per_s", c_f64),
+                ("smem_bytes_per_clk_sm", c_f64), ("fp32_flops_per_s", c_f64),
+                ("fp32_flops_per_clk_sm", c_f64), ("fp64_flops_per_s", c_f64),
+                ("fp64_flops_per_clk_sm", c_f64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PaSystem(ctypes.Structure):
     _fields_ = [("nvars", c_i32), ("axes", ctypes.POINTER(PaAxis)), ("nrel", c_i32),
                 ("rels", ctypes.POINTER(PaRelation)), ("nexposed", c_i32),
@@ -140,7 +151,8 @@ EXPORTS = ["pa_create", "pa_destroy", "pa_last_error", "pa_sync", "pa_array_word
            "pa_mlp_create", "pa_mlp_destroy", "pa_mlp_num_params", "pa_mlp_get_params",
            "pa_mlp_set_params", "pa_mlp_get_grads", "pa_mlp_forward", "pa_mlp_backward",
            "pa_mlp_adam", "pa_join_log", "pa_plan_learned",
-           "pa_set_contract_path", "pa_autotune", "pa_get_rates", "pa_set_rates"]
+           "pa_set_contract_path", "pa_autotune", "pa_get_rates", "pa_set_rates",
+           "pa_measure_peaks", "pa_wait_selftest"]
 
 _lib = None
 
@@ -177,6 +189,10 @@ def load(build_if_missing: bool = True):
     lib.pa_plot.restype = c_i32
     lib.pa_contract.argtypes = [vp, P(PaArray), P(PaArray), c_i32, P(c_i32), P(PaArray), vp]
     lib.pa_contract.restype = c_i32
+    lib.pa_wait_selftest.argtypes = [vp, c_i64, vp]
+    lib.pa_wait_selftest.restype = c_i32
+    lib.pa_measure_peaks.argtypes = [vp, P(PaPeaks), vp]
+    lib.pa_measure_peaks.restype = c_i32
     lib.pa_contract_count.argtypes = [vp, P(PaArray), P(PaArray), c_i32, P(c_i32), vp, vp]
     lib.pa_contract_count.restype = c_i32
     lib.pa_solve_network.argtypes = [vp, c_i32, P(PaAxis), c_i32, P(PaRelation), c_i32, P(c_i32),

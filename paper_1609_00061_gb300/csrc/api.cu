@@ -2173,6 +2173,42 @@ pa_status pa_autotune(pa_ctx* ctx, pa_rates* out, void* stream) {
   return st;
 }
 
+pa_status pa_wait_selftest(pa_ctx* ctx, int64_t limit_ns, void* stream) {
+  if (!ctx || limit_ns < 1000 || limit_ns > 2000000000ll) return PA_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PA_ERR_CUDA, "cudaSetDevice failed");
+  }
+  cudaError_t e = launch_wait_selftest(ctx->d_err, (long long)limit_ns, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return set_err(ctx, PA_ERR_CUDA, cudaGetErrorString(e));
+  return PA_OK;
+}
+
+pa_status pa_measure_peaks(pa_ctx* ctx, pa_peaks* out, void* stream) {
+  if (!ctx || !out) return PA_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, PA_ERR_CUDA, "cudaSetDevice failed");
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (sms <= 0) return set_err(ctx, PA_ERR_CUDA, "multiprocessor count");
+  memset(out, 0, sizeof *out);
+  out->sms = sms;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double clk = 0, clk2 = 0;
+  cudaError_t e = run_probe(0, sms, s, &out->lop3_ops_per_s, &out->lop3_per_clk_sm, &clk);
+  if (e == cudaSuccess)
+    e = run_probe(1, sms, s, &out->smem_bytes_per_s, &out->smem_bytes_per_clk_sm, &clk2);
+  if (e == cudaSuccess)
+    e = run_probe(2, sms, s, &out->fp32_flops_per_s, &out->fp32_flops_per_clk_sm, &clk2);
+  if (e == cudaSuccess)
+    e = run_probe(3, sms, s, &out->fp64_flops_per_s, &out->fp64_flops_per_clk_sm, &clk2);
+  out->sm_clock_hz = clk;
+  if (e != cudaSuccess) return set_err(ctx, PA_ERR_CUDA, std::string("probe: ") + cudaGetErrorString(e));
+  return PA_OK;
+}
+
 pa_status pa_profile_enable(pa_ctx* ctx, int32_t on) {
   if (!ctx) return PA_ERR_INVALID_ARG;
   ctx->prof = on != 0;

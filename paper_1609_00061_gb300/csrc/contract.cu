@@ -703,6 +703,22 @@ cudaError_t rowor_encode_map(const RowOrDesc& d, CUtensorMap* map) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Failure-path check of the bounded waits: one thread waits on an mbarrier
+// that nothing arrives at, gives up after limit_ns as every wait of the
+// contraction kernels does, and sets the error word.
+__global__ void wait_selftest_kernel(int* err, long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_selftest(int* err, long long limit_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
                          const int64_t* d_cta0, int nprob, int64_t grid, size_t smem, int Nt,
                          cudaStream_t s) {

@@ -245,6 +245,11 @@ cudaError_t launch_mma(const MmaDesc* d_descs, const CUtensorMap* d_maps, const 
 // arrays of ndim entries).
 void launch_permute_u32(const uint32_t* in, uint32_t* out, int ndim, const int64_t* d_ext,
                         const int64_t* d_stride, int64_t total, cudaStream_t s);
+// Throughput probe `which` (0: 32-bit LOP3, 1: shared-memory load bytes,
+// 2: FP32 FMA flops, 3: FP64 mul + add flops) over every SM: operations per
+// second, per SM per cycle, and the SM clock it ran at.
+cudaError_t run_probe(int which, int sms, cudaStream_t s, double* per_s, double* per_clk_sm,
+                      double* clock_hz);
 // Random bit rows of the given density (autotuning inputs); padding stays zero.
 void launch_random_bits(uint64_t* w, int64_t nwords, int64_t row_words, int64_t valid,
                         double density, uint64_t seed, cudaStream_t s);
@@ -254,6 +259,8 @@ cudaError_t probe_kernel_image();
 void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
 // *out += number of set bits in w[0..nwords) (padding bits are zero)
 void launch_popcount(const uint64_t* w, int64_t nwords, unsigned long long* out, cudaStream_t s);
+// One bounded mbarrier wait that nothing completes (sets *err after limit_ns).
+cudaError_t launch_wait_selftest(int* err, long long limit_ns, cudaStream_t s);
 
 // ----------------------------------------------------------- host helpers
 int64_t coeff_count(int n, int degree);

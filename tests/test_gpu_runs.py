@@ -74,3 +74,4 @@ def test_runs_banded_b(eng, orc):
     got = eng.contract(pack(A, (0, 1)), pack(B, (1, 2)), (0, 2))
     eng.sync()
     check_same(got, want)
+
