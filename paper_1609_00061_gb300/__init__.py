@@ -274,22 +274,86 @@ def pa_solve_network_static(axes, rels, exposed, out: BitArray, order="greedy", 
     return st.as_dict()
 
 
+def _struct_dtype(ctype, fields):
+    """A numpy dtype laid out exactly like the ctypes Structure `ctype` for the
+    listed (name, numpy type) fields (the others are left as padding)."""
+    names, formats, offsets = [], [], []
+    for name, fmt in fields:
+        names.append(name)
+        formats.append(fmt)
+        offsets.append(getattr(ctype, name).offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets,
+                     "itemsize": ctypes.sizeof(ctype)})
+
+
+_AXIS_DT = _struct_dtype(PaAxis, [("lo", "<f8"), ("hi", "<f8"), ("res", "<i4")])
+_REL_DT = _struct_dtype(PaRelation, [("arity", "<i4"), ("vars", ("<i4", 8)), ("degree", "<i4"),
+                                     ("coeffs", "<u8"), ("kind", "<i4"), ("eps", "<f8"),
+                                     ("expr", "<u8")])
+_SYS_DT = _struct_dtype(PaSystem, [("nvars", "<i4"), ("axes", "<u8"), ("nrel", "<i4"),
+                                   ("rels", "<u8"), ("nexposed", "<i4"), ("exposed", "<u8")])
+
+
 def _systems(systems):
-    """Marshal workloads.System objects; returns (array, keep-alive list)."""
-    arr = (PaSystem * len(systems))()
-    keep = []
-    for k, sy in enumerate(systems):
-        ax = _axes(sy.axes)
-        rl, kc = _relations(sy.rels)
-        ex = _i32(sy.exposed)
-        keep.extend([ax, rl, kc, ex])
-        arr[k].nvars = len(sy.axes)
-        arr[k].axes = ctypes.cast(ax, ctypes.POINTER(PaAxis))
-        arr[k].nrel = len(sy.rels)
-        arr[k].rels = ctypes.cast(rl, ctypes.POINTER(PaRelation))
-        arr[k].nexposed = len(sy.exposed)
-        arr[k].exposed = ctypes.cast(ex, ctypes.POINTER(ctypes.c_int32))
-    return arr, keep
+    """Marshal workloads.System objects into one array each of systems,
+    axes, relations, coefficients and exposed variables (numpy buffers laid
+    out as the C structures); returns (pointer to the systems, keep-alive list)."""
+    n = len(systems)
+    nax = np.array([len(sy.axes) for sy in systems], dtype=np.int64)
+    nrl = np.array([len(sy.rels) for sy in systems], dtype=np.int64)
+    nex = np.array([len(sy.exposed) for sy in systems], dtype=np.int64)
+    axes = np.zeros(max(1, int(nax.sum())), dtype=_AXIS_DT)
+    flat_axes = [a for sy in systems for a in sy.axes]
+    if flat_axes:
+        fa = np.array([(float(a[0]), float(a[1])) for a in flat_axes], dtype=np.float64)
+        axes["lo"][:len(flat_axes)] = fa[:, 0]
+        axes["hi"][:len(flat_axes)] = fa[:, 1]
+        axes["res"][:len(flat_axes)] = [int(a[2]) for a in flat_axes]
+    rels_all = [r for sy in systems for r in sy.rels]
+    coeff_parts = [np.ascontiguousarray(r.coeffs, dtype=np.float64) for r in rels_all]
+    lens = np.array([c.size for c in coeff_parts], dtype=np.int64)
+    coeffs = np.concatenate(coeff_parts) if coeff_parts else np.zeros(1)
+    coff = np.concatenate([[0], np.cumsum(lens)[:-1]]) if len(lens) else np.zeros(0, np.int64)
+    rels = np.zeros(max(1, len(rels_all)), dtype=_REL_DT)
+    m = len(rels_all)
+    if m:
+        ar = np.array([len(r.vars) for r in rels_all], dtype=np.int32)
+        vv = np.zeros((m, 8), dtype=np.int32)
+        for i, r in enumerate(rels_all):
+            vv[i, :len(r.vars)] = r.vars
+        rels["arity"][:m] = ar
+        rels["vars"][:m] = vv
+        rels["degree"][:m] = [int(r.degree) for r in rels_all]
+        rels["coeffs"][:m] = coeffs.ctypes.data + 8 * coff.astype(np.uint64)
+        rels["kind"][:m] = [int(r.kind) for r in rels_all]
+        rels["eps"][:m] = [float(r.eps) for r in rels_all]
+    keep = [axes, rels, coeffs]
+    for i, r in enumerate(rels_all):
+        ex = getattr(r, "expr", None)
+        if ex is not None:
+            ops = np.ascontiguousarray(ex[0], dtype=np.int32)
+            consts = np.ascontiguousarray(ex[1], dtype=np.float64)
+            pe = PaExpr()
+            pe.nops = len(ops)
+            pe.ops = ops.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            pe.nconsts = len(consts)
+            pe.consts = consts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            keep.extend([ops, consts, pe])
+            rels["expr"][i] = ctypes.addressof(pe)
+    exposed = np.array([v for sy in systems for v in sy.exposed] or [0], dtype=np.int32)
+    keep.append(exposed)
+    sysarr = np.zeros(n, dtype=_SYS_DT)
+    ax0 = np.concatenate([[0], np.cumsum(nax)[:-1]]).astype(np.uint64)
+    rl0 = np.concatenate([[0], np.cumsum(nrl)[:-1]]).astype(np.uint64)
+    ex0 = np.concatenate([[0], np.cumsum(nex)[:-1]]).astype(np.uint64)
+    sysarr["nvars"] = nax
+    sysarr["axes"] = axes.ctypes.data + ax0 * np.uint64(_AXIS_DT.itemsize)
+    sysarr["nrel"] = nrl
+    sysarr["rels"] = rels.ctypes.data + rl0 * np.uint64(_REL_DT.itemsize)
+    sysarr["nexposed"] = nex
+    sysarr["exposed"] = exposed.ctypes.data + ex0 * np.uint64(4)
+    keep.append(sysarr)
+    return ctypes.cast(sysarr.ctypes.data, ctypes.POINTER(PaSystem)), keep
 
 
 def _opts(order, strict, model=None, ncand=0):

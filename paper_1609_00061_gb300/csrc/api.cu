@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "mlp.h"
@@ -597,6 +598,21 @@ bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   return t_mma < t_or;
 }
 
+// The occupancy bitmaps of a tensor-core problem (one bit per 128 x 128 tile
+// of each operand), cleared before its expansion kernels set them.
+void add_occupancy(Builder& bd, MmaDesc& md) {
+  const int64_t w32 = mma_occ_words(md);
+  const int64_t w64 = (w32 + 1) / 2;
+  uint32_t* occ = static_cast<uint32_t*>(bd.alloc((size_t)w64 * 8));
+  md.occ_a = occ;
+  md.occ_b = occ + md.nbatch * md.m_tiles * md.kb_words;
+  Op op;
+  op.kind = OP_MEMSET;
+  op.p = reinterpret_cast<uint64_t*>(occ);
+  op.count = w64;
+  bd.ops.push_back(op);
+}
+
 // rx, ry: estimated densities of X and Y (< 0: unknown); *rho_out receives the
 // estimated density of the result when both are known.
 BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int>& keep,
@@ -690,6 +706,7 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     mma_plan(md);
     md.Ab = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.M * md.Kp)));
     md.Bb = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.N * md.Kp)));
+    add_occupancy(bd, md);
     bd.pend_mma.push_back(md);
     bd.st.mma_macs += (double)js.nbatch * (double)js.M * js.nbits * (double)js.K;
     bd.st.n_mma++;
@@ -770,6 +787,7 @@ void join_count(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector
   mma_plan(md);
   md.Ab = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.M * md.Kp)));
   md.Bb = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.N * md.Kp)));
+  add_occupancy(bd, md);
   bd.pend_mma.push_back(md);
   bd.st.mma_macs += nb * M * N * (double)js.K;
   bd.st.n_mma++;
@@ -1126,7 +1144,54 @@ struct Network {
   std::vector<int32_t> own_pairs;  // orders chosen by the learned planner
   std::vector<double> dens_cache;  // estimated plot densities (both passes of a call share them)
   std::vector<uint64_t> slot_keys;  // per slot: key of the relations and kept variables below it
+  Plan plan;                        // the join order, planned once for both passes of a call
+  bool planned = false;
 };
+
+// Run f(i) for i in [0, n) on up to `threads` host threads (contiguous
+// shares; f must not touch shared state).
+template <class F>
+void parallel_for(size_t n, size_t min_per_thread, F&& f) {
+  const size_t hw = std::max<unsigned>(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(std::min<size_t>(hw, 32), (n + min_per_thread - 1) /
+                                                                   std::max<size_t>(1, min_per_thread));
+  if (nt <= 1) {
+    for (size_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (size_t t = 0; t < nt; ++t)
+    pool.emplace_back([&, t]() {
+      for (size_t i = n * t / nt; i < n * (t + 1) / nt; ++i) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
+// The join order of every network not planned yet, in parallel (planning
+// reads only the network's own shapes).
+void plan_networks(std::vector<Network>& nets) {
+  std::vector<size_t> todo;
+  bool heavy = false;
+  for (size_t k = 0; k < nets.size(); ++k)
+    if (!nets[k].planned) {
+      todo.push_back(k);
+      heavy = heavy || nets[k].order == PA_ORDER_OPTIMAL;
+    }
+  parallel_for(todo.size(), heavy ? 1 : 256, [&](size_t i) {
+    Network& n = nets[todo[i]];
+    std::vector<double> vresd(n.nvars);
+    for (int v = 0; v < n.nvars; ++v) vresd[v] = n.axes[v].res;
+    std::vector<std::vector<int>> rv;
+    for (int r = 0; r < n.nrel; ++r) {
+      std::vector<int> d;
+      for (int p = 0; p < n.rels[r].arity; ++p)
+        if (std::find(d.begin(), d.end(), n.rels[r].vars[p]) == d.end()) d.push_back(n.rels[r].vars[p]);
+      rv.push_back(d);
+    }
+    n.plan = plan_joins(n.nvars, vresd, rv, n.exposed, n.order, n.pairs);
+    n.planned = true;
+  });
+}
 
 std::vector<double> plot_densities(const Network& n, pa_ctx* ctx);
 uint64_t relation_key(const pa_relation& r, const pa_axis* axes);
@@ -1182,6 +1247,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
   for (auto& n : nets)
     for (int i = 0; i < n.nrel; ++i) reqs.push_back({&n.rels[i], n.axes, n.strict, nullptr});
   std::vector<BitArr> plots = plot_all(bd, reqs);
+  plan_networks(nets);
 
   struct State {
     Plan plan;
@@ -1202,9 +1268,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
       s.vres[v] = n.axes[v].res;
       vresd[v] = n.axes[v].res;
     }
-    std::vector<std::vector<int>> rv;
-    for (int i = 0; i < n.nrel; ++i) rv.push_back(distinct_vars(n.rels[i]));
-    s.plan = plan_joins(n.nvars, vresd, rv, n.exposed, n.order, n.pairs);
+    s.plan = n.plan;
     for (int i = 0; i < n.nrel; ++i) s.slots.push_back(plots[pidx++]);
     const int nj = (int)s.plan.joins.size();
     s.slots.resize(n.nrel + nj);
@@ -1839,17 +1903,25 @@ std::vector<LearnedChoice> plan_learned(pa_ctx* ctx, Mlp* mlp, const std::vector
   std::vector<Cand> cands;
   std::vector<float> X;
   std::vector<size_t> first(nets.size());
+  // the candidate orders of every network, planned in parallel (pure
+  // functions of the shapes)
+  std::vector<std::vector<Plan>> cplans(nets.size());
+  parallel_for(nets.size(), 1, [&](size_t k) {
+    const Network& n = nets[k];
+    for (int c = 0; c < ncand; ++c)
+      cplans[k].push_back((c == 0)   ? plan_of(n, PA_ORDER_GREEDY, nullptr, 0)
+                          : (c == 1) ? plan_of(n, PA_ORDER_OPTIMAL, nullptr, 0)
+                          : (c == 2) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 1)
+                          : (c == 3) ? plan_of(n, PA_ORDER_LEFT, nullptr, 0)
+                                     : plan_of(n, PA_ORDER_GREEDY, nullptr, 2 + (uint64_t)c * 7919 + k));
+  });
   for (size_t k = 0; k < nets.size(); ++k) {
     const Network& n = nets[k];
     first[k] = cands.size();
     const std::vector<double> dens = plot_densities(n, ctx);
     std::vector<std::vector<int32_t>> seen;
     for (int c = 0; c < ncand; ++c) {
-      Plan p = (c == 0) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 0)
-               : (c == 1) ? plan_of(n, PA_ORDER_OPTIMAL, nullptr, 0)
-               : (c == 2) ? plan_of(n, PA_ORDER_GREEDY, nullptr, 1)
-               : (c == 3) ? plan_of(n, PA_ORDER_LEFT, nullptr, 0)
-                          : plan_of(n, PA_ORDER_GREEDY, nullptr, 2 + (uint64_t)c * 7919 + k);
+      const Plan& p = cplans[k][c];
       std::vector<int32_t> key;
       for (const Join& j : p.joins) {
         key.push_back(j.a);

@@ -146,11 +146,36 @@ __global__ void unpack_rows_kernel(const MmaDesc* __restrict__ descs) {
   const int64_t rows = d.nbatch * d.M, row_words = d.a_row_words, Kp = d.Kp;
   const int64_t cpr = Kp / 16;
   const int64_t total = rows * cpr;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+  // the loop's trip count is the same for every lane of a warp (total is
+  // rounded up to whole warps), so the occupancy ballot sees all 32 lanes
+  const int64_t total_w = (total + 31) / 32 * 32;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_w;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / cpr, c = i - r * cpr, w = c >> 2;
-    const uint64_t word = w < row_words ? __ldg(in + r * row_words + w) : 0ull;
-    reinterpret_cast<uint4*>(out)[i] = expand16((uint32_t)(word >> ((c & 3) * 16)) & 0xFFFFu);
+    uint32_t bits = 0;
+    int64_t r = 0, c = 0;
+    if (i < total) {
+      r = i / cpr;
+      c = i - r * cpr;
+      const int64_t w = c >> 2;
+      const uint64_t word = w < row_words ? __ldg(in + r * row_words + w) : 0ull;
+      bits = (uint32_t)(word >> ((c & 3) * 16)) & 0xFFFFu;
+      reinterpret_cast<uint4*>(out)[i] = expand16(bits);
+    }
+    // one atomic per (row tile, K block) among the lanes whose chunk holds a
+    // set bit: the lowest such lane of each tile and block sets its bit
+    if (d.occ_a) {
+      const bool nzl = bits != 0;
+      const uint32_t nz = __ballot_sync(0xffffffffu, nzl);
+      if (nzl) {
+        const unsigned long long key =
+            (unsigned long long)(((r / d.M) * d.m_tiles + (r % d.M) / 128) * (Kp / 128) + c / 8);
+        const uint32_t peers = __match_any_sync(nz, key);
+        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+          const int64_t tile = (int64_t)key / (Kp / 128), kb = (int64_t)key % (Kp / 128);
+          atomicOr(d.occ_a + tile * d.kb_words + kb / 32, 1u << (kb % 32));
+        }
+      }
+    }
   }
 }
 
@@ -178,6 +203,11 @@ __global__ void unpack_transpose_kernel(const MmaDesc* __restrict__ descs) {
     const uint64_t* src = in + b * K * Nw + nbk;
     uint64_t lo = k0 < K ? __ldg(src + k0 * Nw) : 0ull;
     uint64_t hi = k0 + 32 < K ? __ldg(src + (k0 + 32) * Nw) : 0ull;
+    // a 64 x 64 block lies inside one (column tile, K block) pair
+    if (d.occ_b && __any_sync(0xffffffffu, (lo | hi) != 0ull) && lane == 0) {
+      const int64_t nt = (nbk * 64) / d.BN, kblock = (kb * 64) / 128;
+      atomicOr(d.occ_b + (b * d.n_tiles + nt) * d.kb_words + kblock / 32, 1u << (kblock % 32));
+    }
     transpose64(lo, hi, lane);
     uint8_t* dst = out + (b * N) * Kp + kb * 64;
     const int sub = lane >> 2, c = lane & 3;
@@ -249,6 +279,19 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
   const int BN = d.BN;
   const int stage_bytes = kMmaATile + BN * kMmaBK;
   const int nk = (int)(d.Kp / kMmaBK);
+  // the K blocks where both this CTA's A row tile and B column tile hold a set
+  // bit (every block when the problem has no occupancy bitmaps); producer and
+  // issuer walk the same sequence, the j-th active block using ring slot j
+  const uint32_t* occa = d.occ_a ? d.occ_a + (b * d.m_tiles + mt) * d.kb_words : nullptr;
+  const uint32_t* occb = d.occ_b ? d.occ_b + (b * d.n_tiles + nt) * d.kb_words : nullptr;
+  const int kbw = (nk + 31) / 32;
+  auto active = [&](int w) -> uint32_t {
+    uint32_t m = 0xffffffffu;
+    if (occa) m &= __ldg(occa + w);
+    if (occb) m &= __ldg(occb + w);
+    if (w == kbw - 1 && (nk & 31)) m &= (1u << (nk & 31)) - 1u;
+    return m;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -257,60 +300,73 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
       // the tensor maps were written to global memory by a copy before the launch
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma) : "memory");
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb) : "memory");
-      for (int k = 0; k < nk; ++k) {
-        const int s = k % kMmaStages;
-        const uint32_t ph = (uint32_t)(k / kMmaStages) & 1u;
-        if (k >= kMmaStages && !bar_wait(&empty[s], ph ^ 1u)) {
-          *sfail = 1;
-          break;
+      int j = 0;
+      bool failed = false;
+      for (int w = 0; w < kbw && !failed; ++w) {
+        for (uint32_t m = active(w); m; m &= m - 1) {
+          const int k = w * 32 + __ffs(m) - 1;
+          const int s = j % kMmaStages;
+          const uint32_t ph = (uint32_t)(j / kMmaStages) & 1u;
+          if (j >= kMmaStages && !bar_wait(&empty[s], ph ^ 1u)) {
+            *sfail = 1;
+            failed = true;
+            break;
+          }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                           smem_addr(&full[s])),
+                       "r"(stage_bytes)
+                       : "memory");
+          const uint32_t dst_a = smem_addr(smem + (size_t)s * kMmaStageMax);
+          const uint32_t dst_b = dst_a + kMmaATile;
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst_a),
+              "l"(reinterpret_cast<uint64_t>(ma)), "r"(k * kMmaBK), "r"((int)(mt * kMmaBM)),
+              "r"((int)b), "r"(smem_addr(&full[s]))
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst_b),
+              "l"(reinterpret_cast<uint64_t>(mb)), "r"(k * kMmaBK), "r"((int)(nt * BN)),
+              "r"((int)b), "r"(smem_addr(&full[s]))
+              : "memory");
+          ++j;
         }
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                         smem_addr(&full[s])),
-                     "r"(stage_bytes)
-                     : "memory");
-        const uint32_t dst_a = smem_addr(smem + (size_t)s * kMmaStageMax);
-        const uint32_t dst_b = dst_a + kMmaATile;
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst_a),
-            "l"(reinterpret_cast<uint64_t>(ma)), "r"(k * kMmaBK), "r"((int)(mt * kMmaBM)),
-            "r"((int)b), "r"(smem_addr(&full[s]))
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst_b),
-            "l"(reinterpret_cast<uint64_t>(mb)), "r"(k * kMmaBK), "r"((int)(nt * BN)), "r"((int)b),
-            "r"(smem_addr(&full[s]))
-            : "memory");
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = f8_idesc(kMmaBM, BN);
-      for (int k = 0; k < nk; ++k) {
-        const int s = k % kMmaStages;
-        const uint32_t ph = (uint32_t)(k / kMmaStages) & 1u;
-        if (!bar_wait(&full[s], ph)) {
-          *sfail = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_addr(smem + (size_t)s * kMmaStageMax), b0 = a0 + kMmaATile;
+      int j = 0;
+      bool failed = false;
+      for (int w = 0; w < kbw && !failed; ++w) {
+        for (uint32_t m = active(w); m; m &= m - 1) {
+          const int s = j % kMmaStages;
+          const uint32_t ph = (uint32_t)(j / kMmaStages) & 1u;
+          if (!bar_wait(&full[s], ph)) {
+            *sfail = 1;
+            failed = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_addr(smem + (size_t)s * kMmaStageMax), b0 = a0 + kMmaATile;
 #pragma unroll
-        for (int kk = 0; kk < kMmaBK / 32; ++kk) {
-          const uint64_t ad = sw128_kmajor_desc(a0 + kk * 32), bd = sw128_kmajor_desc(b0 + kk * 32);
-          const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+          for (int kk = 0; kk < kMmaBK / 32; ++kk) {
+            const uint64_t ad = sw128_kmajor_desc(a0 + kk * 32), bd = sw128_kmajor_desc(b0 + kk * 32);
+            const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
           asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_addr(&empty[s]))
               : "memory");
+          ++j;
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&empty[s]))
-            : "memory");
       }
       // arrives once every MMA issued above has completed (also on failure)
       asm volatile(
@@ -323,21 +379,41 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
     const int ew = warp - 4;
     const bool ok = bar_wait(accum, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // no K block in common: nothing was accumulated, every sum is zero
+    bool none = true;
+    for (int w = 0; w < kbw && none; ++w) none = (active(w) == 0);
     const int64_t m = mt * kMmaBM + ew * 32 + lane;
     for (int c = 0; c < BN / 64; ++c) {
       uint32_t v[64];
       const uint32_t ta = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(c * 64);
-      tmem_ld32(ta, v);
-      tmem_ld32(ta + 32u, v + 32);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (d.counts) {
-        // counting semiring: every sum is an integer <= K <= 2^24, exact in FP32
-        const int64_t n0 = nt * BN + c * 64;
-        if (ok && !*sfail && m < d.M) {
-          uint32_t* row = d.counts + (b * d.M + m) * d.N;
+      if (none) {
 #pragma unroll
-          for (int j = 0; j < 64; ++j)
-            if (n0 + j < d.N) row[n0 + j] = (uint32_t)__uint_as_float(v[j]);
+        for (int j = 0; j < 64; ++j) v[j] = 0u;
+      } else {
+        tmem_ld32(ta, v);
+        tmem_ld32(ta + 32u, v + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      if (d.counts) {
+        // counting semiring: every sum is an integer <= K <= 2^24, exact in
+        // FP32.  The warp's 32 rows x 64 counts go through shared memory (the
+        // operand ring is idle once every product is done; rows padded to 65
+        // words against bank conflicts) so that each store writes 32
+        // consecutive counts of one row.
+        if (ok && !*sfail) {
+          uint32_t* st = reinterpret_cast<uint32_t*>(smem) + ew * (32 * 65);
+#pragma unroll
+          for (int j = 0; j < 64; ++j) st[lane * 65 + j] = (uint32_t)__uint_as_float(v[j]);
+          __syncwarp();
+          const int64_t n0 = nt * BN + c * 64;
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t mm = mt * kMmaBM + ew * 32 + rr;
+            if (mm >= d.M) break;
+            uint32_t* row = d.counts + (b * d.M + mm) * d.N;
+            if (n0 + lane < d.N) row[n0 + lane] = st[rr * 65 + lane];
+            if (n0 + 32 + lane < d.N) row[n0 + 32 + lane] = st[rr * 65 + 32 + lane];
+          }
+          __syncwarp();
         }
         continue;
       }
@@ -426,6 +502,11 @@ void mma_plan(MmaDesc& d) {
   d.Kp = (d.K + kMmaBK - 1) / kMmaBK * kMmaBK;
   d.m_tiles = (d.M + kMmaBM - 1) / kMmaBM;
   d.n_tiles = (d.N + d.BN - 1) / d.BN;
+  d.kb_words = (d.Kp / kMmaBK + 31) / 32;
+}
+
+int64_t mma_occ_words(const MmaDesc& d) {
+  return d.nbatch * (d.m_tiles + d.n_tiles) * d.kb_words;
 }
 
 int64_t mma_ctas(const MmaDesc& d) { return d.nbatch * d.m_tiles * d.n_tiles; }

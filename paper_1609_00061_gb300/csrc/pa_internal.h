@@ -223,7 +223,16 @@ struct MmaDesc {
   int* err;                   // device error word: set when a bounded wait runs out
   uint32_t* counts;           // when not null: the sums themselves, [nbatch][M][N]
                               // (counting semiring), and C is not written
+  // Occupancy bitmaps of the 128 x 128 tiles (cleared before the expansion,
+  // set by it): bit kb of occ_a[(b * m_tiles + mt) * kb_words + kb / 32] when
+  // A's rows 128 mt.. and K values 128 kb.. hold a set bit, likewise occ_b per
+  // BN-column tile.  The contraction multiplies only the K blocks both hold.
+  uint32_t* occ_a;
+  uint32_t* occ_b;
+  int64_t kb_words;
 };
+// 32-bit words of the two occupancy bitmaps of a planned problem
+int64_t mma_occ_words(const MmaDesc& d);
 void mma_plan(MmaDesc& d);    // BN, Nw, Kp and the tile counts from M, N, K, nbatch
 int64_t mma_ctas(const MmaDesc& d);
 size_t mma_smem_bytes();
