@@ -337,7 +337,9 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
 
     usable = L.usable_networks
     t0 = time.perf_counter()
+    # training networks of both wirings (disjoint seeds from the evaluation sets)
     train = usable(W.random_networks(n_train, seed=W.SEED_BASE + 50))
+    train += usable(W.random_networks(n_train // 2, seed=W.SEED_BASE + 51, window=8))
     X, T, D = L.collect_logs(eng, train, orders_per_system=3, seed=2)
     model = pa.CostModel(eng, hidden=128, nlayers=3, seed=W.SEED_BASE + 5)
     hist = model.train(X, T, epochs=150, batch=256, lr=2e-3)
@@ -351,7 +353,7 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     torch.cuda.synchronize()
     judge_log_s = time.perf_counter() - t0
 
-    def time_batch(order):
+    def time_batch(order, nets=nets):
         t0 = time.perf_counter()
         b = eng.batch(nets, order=order, model=model if order == "learned" else None)
         b.run()
@@ -374,6 +376,17 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
     o_s, o_st = time_batch("optimal")
     l_s, l_st = time_batch("learned")
     _, learned_flags, pred = eng.plan_learned(model, nets)
+    # the same generator with relations drawn from windows of 8 consecutive
+    # variables instead of 4: looser wirings, where the greedy order is far
+    # from the least naive cost on a fifth of the networks
+    wide = usable(W.random_networks(256, seed=W.SEED_BASE + 6, window=8))
+    for n in wide:
+        eng.log_joins(n)
+    torch.cuda.synchronize()
+    wg_s, wg_st = time_batch("greedy", wide)
+    wo_s, wo_st = time_batch("optimal", wide)
+    wl_s, wl_st = time_batch("learned", wide)
+    _, wide_flags, _ = eng.plan_learned(model, wide)
     outs = [pa.BitArray.empty(n.exposed, [n.axes[v][2] for v in n.exposed], eng.device)
             for n in nets]
     for n, o in zip(nets[:16], outs[:16]):
@@ -411,6 +424,19 @@ def run_learned(eng, pa, W, n_eval=512, n_train=64, reps=3):
             "pixel_ops_dense_learned": l_st["pixel_ops_dense"],
             "graph_launches": {"greedy": g_st["n_launches"], "optimal": o_st["n_launches"],
                                "learned": l_st["n_launches"]},
+            "wide_windows": {
+                "workload": "the same generator, relations from windows of 8 consecutive "
+                            "variables, seed 0x160900061+6, 256 drawn",
+                "networks": len(wide),
+                "batched_greedy_systems_per_s": len(wide) / wg_s,
+                "batched_optimal_systems_per_s": len(wide) / wo_s,
+                "batched_learned_systems_per_s": len(wide) / wl_s,
+                "learned_vs_batched_greedy": wg_s / wl_s,
+                "optimal_vs_batched_greedy": wg_s / wo_s,
+                "learned_orders_kept": int(sum(wide_flags)),
+                "pixel_ops_dense": {"greedy": wg_st["pixel_ops_dense"],
+                                    "optimal": wo_st["pixel_ops_dense"],
+                                    "learned": wl_st["pixel_ops_dense"]}},
             "timing": "batched: CUDA events around graph replays; plain: host clock, "
                       "synchronised; fresh: host clock around planning, capture and the "
                       "first replay"}
