@@ -585,6 +585,15 @@ def run_ours(args, rank, world, local_rank):
     ms_max, ops_per_ms = whole_job(ms, ops, world, dist, f"cuda:{dev}")
     value = ops_per_ms * 1e3 / 1e9
 
+    # host cost of one call (the program is kept, so this is argument checks,
+    # the descriptor upload and the launches): back-to-back calls, host clock
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        step()
+    host_us = (time.perf_counter() - t0) / 200 * 1e6
+    torch.cuda.synchronize()
+
     # end to end through the public call: host coefficients in, output words out
     host_out = torch.empty(out.words.numel(), dtype=torch.int64, pin_memory=True)
     h2d = sum(r.coeffs.nbytes for r in sysm.rels) + 20 * len(sysm.axes)
@@ -613,6 +622,7 @@ def run_ours(args, rank, world, local_rank):
                    "pixel_ops_per_step": ops, "parallelism": f"independent systems x{world}",
                    "contract_path": args.path, "tensor_core_joins": int(st["n_mma"]),
                    "autotuned_rates": rates,
+                   "host_us_per_call": host_us,
                    "observed_join_densities": [round(float(x), 5) for x in observed]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(out.words.numel() * 8)},

@@ -87,8 +87,8 @@ pa_status set_err(pa_ctx* ctx, pa_status st, const std::string& msg) {
 bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
 // ------------------------------------------------------------ program
-enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_AND, OP_ROWOR, OP_OUTER, OP_DOT, OP_UNPACK,
-              OP_MMA, OP_CENTRES, OP_PLOT_EXPR, OP_PERMUTE };
+enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_ROWOR, OP_UNPACK,
+              OP_MMA, OP_CENTRES, OP_PLOT_EXPR, OP_PERMUTE, OP_EWISE };
 
 struct Op {
   OpKind kind;
@@ -102,7 +102,6 @@ struct Op {
   uint64_t* p = nullptr;                // memset / and output
   const uint64_t* a = nullptr;
   const uint64_t* b = nullptr;
-  ReshapeDesc rd;
   int join = -1;                        // join this op belongs to (join logging)
 };
 
@@ -112,14 +111,12 @@ const char* op_name(const Op& op) {
     case OP_CENTRES: return "plot_centres_kernel";
     case OP_PLOT_EXPR: return "plot_expr_kernel";
     case OP_PERMUTE: return "permute_u32_kernel";
+    case OP_EWISE: return "ewise_kernel";
     case OP_MEMSET: return "memset";
     case OP_RESHAPE:
-      return op.rd.mode == kReshapeTranspose ? "reshape_transpose_kernel"
-             : op.rd.mode == kReshapeWords   ? "reshape_words_kernel"
-                                             : "reshape_kernel";
-    case OP_AND: return "and_kernel";
-    case OP_OUTER: return "outer_kernel";
-    case OP_DOT: return op.nw > 16 ? "dot_wide_kernel" : "dot_kernel";
+      return op.i0 == kRsTranspose ? "reshape_transpose_kernel"
+             : (op.i0 == kRsWords32 || op.i0 == kRsWords64) ? "reshape_words_kernel"
+                                                            : "reshape_kernel";
     case OP_UNPACK: return "unpack_kernels";
     case OP_MMA: return "mma_bool_kernel";
     default: return "rowor_kernel";
@@ -149,6 +146,14 @@ struct Builder {
   unsigned long long* d_stat = nullptr;
   std::vector<RowOrDesc> pend;  // contractions waiting for one shared launch
   std::vector<MmaDesc> pend_mma;  // tensor-core contractions waiting for one launch
+  // Inside one tree level of build_networks: reshapes wait for one launch per
+  // kind, and the level's other ops for after them (they read the reshapes'
+  // results), so independent joins share launches.
+  bool defer = false;
+  std::vector<ReshapeDesc> pend_rs;
+  std::vector<EwJob> pend_ew;
+  std::vector<Op> pend_ops;
+  void emit(const Op& op) { (defer ? pend_ops : ops).push_back(op); }
 
   Builder(pa_ctx* c, bool dry_, char* base_, size_t blob_cap_)
       : ctx(c), dry(dry_), base(base_), used(blob_cap_), blob_cap(blob_cap_) {}
@@ -297,6 +302,36 @@ void choose_reshape_mode(ReshapeDesc& d, const BitArr& in, const BitArr& out) {
   d.t_out_J = out_word_stride(out, J);
 }
 
+void flush_reshapes(Builder& bd);
+
+// The waiting outer / dot / Hadamard clusters as one launch (job table and
+// block offsets in the blob).
+void flush_ew(Builder& bd) {
+  std::vector<EwJob> jobs;
+  std::vector<int64_t> cta0(1, 0);
+  for (const EwJob& j : bd.pend_ew) {
+    const int64_t nb = ewise_blocks(j);
+    if (nb <= 0) continue;
+    jobs.push_back(j);
+    cta0.push_back(cta0.back() + nb);
+  }
+  bd.pend_ew.clear();
+  if (jobs.empty()) return;
+  if (cta0.back() > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "cluster grid too large");
+  Op op;
+  op.kind = OP_EWISE;
+  op.off0 = bd.put(jobs.data(), jobs.size(), 64);
+  op.off1 = bd.put(cta0.data(), cta0.size(), 16);
+  op.n = (int)jobs.size();
+  op.count = cta0.back();
+  bd.ops.push_back(op);
+}
+
+void add_ew(Builder& bd, const EwJob& j) {
+  bd.pend_ew.push_back(j);
+  if (!bd.defer) flush_ew(bd);
+}
+
 // out <- in with axes matched by variable; input axes missing from out are
 // OR-reduced, output axes missing from in are broadcast.
 void reshape(Builder& bd, const BitArr& in, const BitArr& out) {
@@ -335,10 +370,35 @@ void reshape(Builder& bd, const BitArr& in, const BitArr& out) {
   }
   choose_reshape_mode(d, in, out);
   bd.st.n_reshapes++;
-  Op op;
-  op.kind = OP_RESHAPE;
-  op.rd = d;
-  bd.ops.push_back(op);
+  bd.pend_rs.push_back(d);
+  if (!bd.defer) flush_reshapes(bd);
+}
+
+// The waiting reshapes as one launch per kernel kind (descriptor table and
+// block offsets in the blob).
+void flush_reshapes(Builder& bd) {
+  for (int kind = 0; kind < 4; ++kind) {
+    std::vector<ReshapeDesc> group;
+    std::vector<int64_t> cta0(1, 0);
+    for (const ReshapeDesc& d : bd.pend_rs) {
+      if (reshape_kind(d) != kind) continue;
+      const int64_t nb = reshape_blocks(d);
+      if (nb <= 0) continue;
+      group.push_back(d);
+      cta0.push_back(cta0.back() + nb);
+    }
+    if (group.empty()) continue;
+    if (cta0.back() > 0x7fffffffLL) bd.fail(PA_ERR_TOO_LARGE, "reshape grid too large");
+    Op op;
+    op.kind = OP_RESHAPE;
+    op.off0 = bd.put(group.data(), group.size(), 64);
+    op.off1 = bd.put(cta0.data(), cta0.size(), 16);
+    op.n = (int)group.size();
+    op.count = cta0.back();
+    op.i0 = kind;
+    bd.ops.push_back(op);
+  }
+  bd.pend_rs.clear();
 }
 
 // Bring `x` into layout `want` (vars/res/inner of want; want.w ignored).  Returns
@@ -407,6 +467,16 @@ void flush_rowor_only(Builder& bd);
 void flush_rowor(Builder& bd) {
   flush_rowor_only(bd);
   flush_mma(bd);
+}
+
+// End of one tree level: its reshapes, then the ops that read them, then the
+// contraction launches.
+void flush_level(Builder& bd) {
+  flush_reshapes(bd);
+  bd.ops.insert(bd.ops.end(), bd.pend_ops.begin(), bd.pend_ops.end());
+  bd.pend_ops.clear();
+  flush_ew(bd);
+  flush_rowor(bd);
 }
 
 void flush_rowor_only(Builder& bd) {
@@ -610,7 +680,7 @@ void add_occupancy(Builder& bd, MmaDesc& md) {
   op.kind = OP_MEMSET;
   op.p = reinterpret_cast<uint64_t*>(occ);
   op.count = w64;
-  bd.ops.push_back(op);
+  bd.emit(op);
 }
 
 // rx, ry: estimated densities of X and Y (< 0: unknown); *rho_out receives the
@@ -637,13 +707,7 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     BitArr ya = conform(bd, Y, make_arr(wv, vres, want.inner));
     BitArr out = want;
     if (!out.w) out.w = bd.alloc_words(out.words());
-    Op op;
-    op.kind = OP_AND;
-    op.a = xa.w;
-    op.b = ya.w;
-    op.p = out.w;
-    op.count = out.words();
-    bd.ops.push_back(op);
+    add_ew(bd, EwJob{xa.w, ya.w, out.w, out.words(), 1, 1, kEwAnd});
     return out;
   }
 
@@ -655,15 +719,7 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     BitArr C = make_arr(js.c_axes, vres, js.ninner);
     if (target && target->w && same_layout(C, *target)) C.w = target->w;
     else C.w = bd.alloc_words(C.words());
-    Op op;
-    op.kind = OP_OUTER;
-    op.a = Am.w;
-    op.b = Bm.w;
-    op.p = C.w;
-    op.count = js.nbatch * js.M;
-    op.m = js.M;
-    op.nw = Bm.row_words();
-    bd.ops.push_back(op);
+    add_ew(bd, EwJob{Am.w, Bm.w, C.w, js.nbatch * js.M, js.M, Bm.row_words(), kEwOuter});
     bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
     return C;
   }
@@ -673,15 +729,16 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     BitArr C = make_arr(js.c_axes, vres, (int)js.c_axes.size());
     if (target && target->w && same_layout(C, *target)) C.w = target->w;
     else C.w = bd.alloc_words(C.words());
-    Op op;
-    op.kind = OP_DOT;
-    op.a = Am.w;
-    op.b = Bm.w;
-    op.p = C.w;
-    op.count = js.nbatch * js.M;
-    op.m = js.M;
-    op.nw = Am.row_words();
-    bd.ops.push_back(op);
+    const int64_t rows = js.nbatch * js.M, kw = Am.row_words();
+    if (kw > 16) {
+      // long rows OR their bits into a cleared C
+      Op z;
+      z.kind = OP_MEMSET;
+      z.p = C.w;
+      z.count = (rows + 63) / 64;
+      bd.emit(z);
+    }
+    add_ew(bd, EwJob{Am.w, Bm.w, C.w, rows, js.M, kw, kw > 16 ? kEwDotWide : kEwDot});
     bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
     return C;
   }
@@ -733,7 +790,7 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     op.kind = OP_MEMSET;
     op.p = C.w;
     op.count = C.words();
-    bd.ops.push_back(op);
+    bd.emit(op);
   }
   bd.pend.push_back(d);
   bd.st.peak_words = std::max<int64_t>(bd.st.peak_words, C.words());
@@ -1302,6 +1359,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
       for (size_t t = 0; t < S[k].plan.joins.size(); ++t)
         n_in_level += (S[k].level[nets[k].nrel + t] == lv);
     const int64_t target_ctas = std::max<int64_t>(1, 152 / std::max(1, n_in_level));
+    bd.defer = !one_join_per_launch;
     for (size_t k = 0; k < nets.size(); ++k) {
       State& s = S[k];
       const int nrel = nets[k].nrel, nj = (int)s.plan.joins.size();
@@ -1328,12 +1386,18 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
         }
       }
     }
-    flush_rowor(bd);
+    flush_level(bd);
+    bd.defer = false;
   }
+  // the final reshapes into the callers' arrays: one launch per kind for all
+  // systems
+  bd.defer = !one_join_per_launch;
   for (size_t k = 0; k < nets.size(); ++k) {
     const BitArr& root = S[k].slots[S[k].plan.root];
     if (root.w != nets[k].target.w) reshape(bd, root, nets[k].target);
   }
+  flush_level(bd);
+  bd.defer = false;
   if (!one_join_per_launch) fold_memsets(bd);
 }
 
@@ -1368,6 +1432,10 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
                     op.i1, op.i2, op.i3, op.m, reinterpret_cast<const ZeroRange*>(blob + op.off1),
                     (int)op.nw, op.zw, s);
         break;
+      case OP_EWISE:
+        launch_ewise(reinterpret_cast<const EwJob*>(blob + op.off0),
+                     reinterpret_cast<const int64_t*>(blob + op.off1), op.n, op.count, s);
+        break;
       case OP_PERMUTE:
         launch_permute_u32(reinterpret_cast<const uint32_t*>(op.a), reinterpret_cast<uint32_t*>(op.p),
                            op.n, reinterpret_cast<const int64_t*>(blob + op.off0),
@@ -1383,16 +1451,8 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
         check_cuda(ctx, cudaMemsetAsync(op.p, 0, (size_t)op.count * 8, s), "cudaMemsetAsync");
         break;
       case OP_RESHAPE:
-        launch_reshape(op.rd, s);
-        break;
-      case OP_AND:
-        launch_and(op.a, op.b, op.p, op.count, s);
-        break;
-      case OP_OUTER:
-        launch_outer(op.a, op.b, op.p, op.count, op.m, op.nw, s);
-        break;
-      case OP_DOT:
-        launch_dot(op.a, op.b, op.p, op.count, op.m, op.nw, s);
+        launch_reshape(reinterpret_cast<const ReshapeDesc*>(blob + op.off0),
+                       reinterpret_cast<const int64_t*>(blob + op.off1), op.n, op.i0, op.count, s);
         break;
       case OP_UNPACK:
         launch_unpack(reinterpret_cast<const MmaDesc*>(blob + op.off0), op.n, op.m, op.nw, s);

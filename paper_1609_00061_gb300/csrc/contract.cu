@@ -13,26 +13,52 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "pa_internal.h"
 
 namespace pa {
 
 // --------------------------------------------------------------- reshape
+// Every reshape launch runs a table of descriptors: problem p owns blocks
+// [cta0[p], cta0[p+1]) and its descriptor is copied into shared memory; the
+// kernels' grid-stride loops run over the problem's own blocks.  (One launch
+// per kind serves all reshapes of one tree level of every system of a batch.)
+struct RsCtx {
+  int64_t bid, nblk;
+};
+__device__ __forceinline__ RsCtx rs_pick(const ReshapeDesc* __restrict__ descs,
+                                         const int64_t* __restrict__ cta0, int n, ReshapeDesc* sd) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta0[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int64_t* src = reinterpret_cast<const int64_t*>(descs + lo);
+  int64_t* dst = reinterpret_cast<int64_t*>(sd);
+  for (int i = threadIdx.x; i < (int)(sizeof(ReshapeDesc) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return RsCtx{(int64_t)blockIdx.x - cta0[lo], cta0[lo + 1] - cta0[lo]};
+}
+
 // Bit mode: one warp per output word, one lane per bit (two ballots pack the
 // 64 bits).  Every bit is decoded and gathered on its own, OR-ed over the
 // reduced axes with an early exit.  With row_any set, every packed input axis
 // is reduced and red_* hold only the reduced row axes: a bit is then the OR of
 // whole input rows, scanned by words (padding bits are zero).
-__global__ void reshape_kernel(const ReshapeDesc d) {
+__global__ void reshape_kernel(const ReshapeDesc* __restrict__ descs, const int64_t* __restrict__ cta0,
+                               int n) {
+  __shared__ ReshapeDesc sd;
+  const RsCtx rc = rs_pick(descs, cta0, n, &sd);
+  const ReshapeDesc& d = sd;
   const int lane = threadIdx.x & 31;
   const int64_t total = d.out_nrows * d.out_row_words;
   const int outer = d.out_ndim - d.out_inner;
   int64_t red_total = 1;
   for (int q = 0; q < d.nred; ++q) red_total *= d.red_res[q];
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t ow = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ow < total;
-       ow += nwarps) {
+  const int64_t nwarps = rc.nblk * (blockDim.x >> 5);
+  for (int64_t ow = rc.bid * (blockDim.x >> 5) + (threadIdx.x >> 5); ow < total; ow += nwarps) {
     const int64_t orow = ow / d.out_row_words, w = ow % d.out_row_words;
     int64_t brow = 0, bcol = 0, rest = orow;
     for (int a = outer - 1; a >= 0; --a) {
@@ -84,11 +110,15 @@ __global__ void reshape_kernel(const ReshapeDesc d) {
 // decomposition (u_res, u_in), then an OR over the reduced axes.  Index type I
 // is 32-bit when every word index fits.
 template <class I>
-__global__ void reshape_words_kernel(const ReshapeDesc d) {
+__global__ void reshape_words_kernel(const ReshapeDesc* __restrict__ descs,
+                                     const int64_t* __restrict__ cta0, int n) {
+  __shared__ ReshapeDesc sd;
+  const RsCtx rc = rs_pick(descs, cta0, n, &sd);
+  const ReshapeDesc& d = sd;
   const I total = (I)(d.out_nrows * d.out_row_words);
   I red_total = 1;
   for (int q = 0; q < d.nred; ++q) red_total *= (I)d.red_res[q];
-  for (I ow = (I)blockIdx.x * blockDim.x + threadIdx.x; ow < total; ow += (I)gridDim.x * blockDim.x) {
+  for (I ow = (I)rc.bid * blockDim.x + threadIdx.x; ow < total; ow += (I)rc.nblk * blockDim.x) {
     I rest = ow, src = 0;
     for (int a = d.nu - 1; a >= 0; --a) {
       const I r = (I)d.u_res[a];
@@ -144,13 +174,17 @@ __device__ __forceinline__ void transpose64(uint64_t& lo, uint64_t& hi, int lane
 // coalesced 32-byte stores of 256 output rows.  Rows of the shared tiles are
 // padded to 5 words so the column reads of a block are free of bank conflicts.
 constexpr int kTrPad = 5;
-__global__ void __launch_bounds__(256) reshape_transpose_kernel(const ReshapeDesc d) {
+__global__ void __launch_bounds__(256)
+reshape_transpose_kernel(const ReshapeDesc* __restrict__ descs, const int64_t* __restrict__ cta0, int n) {
+  __shared__ ReshapeDesc sd;
+  const RsCtx rc = rs_pick(descs, cta0, n, &sd);
+  const ReshapeDesc& d = sd;
   __shared__ uint64_t s_in[256 * kTrPad];
   __shared__ uint64_t s_out[256 * kTrPad];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t nJT = (d.tQ + 255) / 256, nLT = (d.tR + 255) / 256;
   const int64_t tiles = d.n_other * nJT * nLT;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  for (int64_t tile = rc.bid; tile < tiles; tile += rc.nblk) {
     const int64_t lt = tile % nLT, r = tile / nLT, jt = r % nJT;
     int64_t rest = r / nJT, base_in = 0, base_out = 0;
     for (int a = d.nu - 1; a >= 0; --a) {
@@ -190,122 +224,126 @@ __global__ void __launch_bounds__(256) reshape_transpose_kernel(const ReshapeDes
   }
 }
 
-void launch_reshape(const ReshapeDesc& d, cudaStream_t s) {
-  const int64_t total = d.out_nrows * d.out_row_words;
-  if (total <= 0) return;
-  if (d.mode == kReshapeTranspose) {
-    const int64_t tiles = d.n_other * ((d.tQ + 255) / 256) * ((d.tR + 255) / 256);
-    reshape_transpose_kernel<<<(unsigned)std::min<int64_t>(tiles, 152 * 8), 256, 0, s>>>(d);
-    return;
-  }
-  int64_t blocks = (total + 255) / 256;
+int reshape_kind(const ReshapeDesc& d) {
+  if (d.mode == kReshapeTranspose) return kRsTranspose;
   if (d.mode == kReshapeWords) {
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int64_t total = d.out_nrows * d.out_row_words;
+    const int64_t blocks = reshape_blocks(d);
     int64_t in_max = 0;  // largest input word index + 1 (bounded by the sum below)
     for (int a = 0; a < d.nu; ++a) in_max += (d.u_res[a] - 1) * d.u_in[a];
     for (int q = 0; q < d.nred; ++q) in_max += (d.red_res[q] - 1) * d.red_in_w[q];
-    if (total + 256 * blocks < (1ll << 31) && in_max < (1ll << 31))
-      reshape_words_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(d);
-    else
-      reshape_words_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(d);
-    return;
+    return (total + 256 * blocks < (1ll << 31) && in_max < (1ll << 31)) ? kRsWords32 : kRsWords64;
   }
-  blocks = (total + 7) / 8;  // one warp per word
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  reshape_kernel<<<(unsigned)blocks, 256, 0, s>>>(d);
+  return kRsBits;
 }
 
-// ----------------------------------------------------------------- outer
-// C[r][w] = bit r of A ? B[r / M][w] : 0, one thread per output word.
-template <class I>
-__global__ void outer_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
-                             uint64_t* __restrict__ C, I rows, I M, I Nw) {
-  const I total = rows * Nw;
-  for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (I)gridDim.x * blockDim.x) {
-    const I r = i / Nw, w = i - r * Nw;
-    const uint64_t bit = (A[r >> 6] >> (r & 63)) & 1ull;
-    C[i] = bit ? B[(r / M) * Nw + w] : 0ull;
-  }
+int64_t reshape_blocks(const ReshapeDesc& d) {
+  const int64_t total = d.out_nrows * d.out_row_words;
+  if (total <= 0) return 0;
+  if (d.mode == kReshapeTranspose)
+    return std::min<int64_t>(d.n_other * ((d.tQ + 255) / 256) * ((d.tR + 255) / 256), 152 * 8);
+  if (d.mode == kReshapeWords) return std::min<int64_t>((total + 255) / 256, 152 * 16);
+  return std::min<int64_t>((total + 7) / 8, 152 * 16);  // one warp per word
 }
 
-void launch_outer(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
-                  int64_t Nw, cudaStream_t s) {
-  const int64_t total = rows * Nw;
-  if (total <= 0) return;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (total + 256 * blocks < (1ll << 31))
-    outer_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(A, B, C, (uint32_t)rows, (uint32_t)M,
-                                                             (uint32_t)Nw);
-  else
-    outer_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(A, B, C, rows, M, Nw);
-}
-
-// ------------------------------------------------------------------- dot
-// One warp per 64-bit word of C: lanes take bits r and r + 32, AND their A
-// row with the batch's B row word by word, and two ballots pack the bits.
-__global__ void dot_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
-                           uint64_t* __restrict__ C, int64_t rows, int64_t M, int64_t Kw) {
-  const int lane = threadIdx.x & 31;
-  const int64_t words = (rows + 63) / 64;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t cw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cw < words;
-       cw += nwarps) {
-    uint32_t half[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t r = cw * 64 + h * 32 + lane;
-      uint64_t acc = 0;
-      if (r < rows) {
-        const uint64_t* a = A + r * Kw;
-        const uint64_t* b = B + (r / M) * Kw;
-        for (int64_t w = 0; w < Kw && !acc; ++w) acc = a[w] & b[w];
-      }
-      half[h] = __ballot_sync(0xffffffffu, acc != 0);
-    }
-    if (lane == 0) C[cw] = (uint64_t)half[0] | ((uint64_t)half[1] << 32);
+void launch_reshape(const ReshapeDesc* d_descs, const int64_t* d_cta0, int n, int kind,
+                    int64_t grid, cudaStream_t s) {
+  if (n <= 0 || grid <= 0) return;
+  switch (kind) {
+    case kRsTranspose:
+      reshape_transpose_kernel<<<(unsigned)grid, 256, 0, s>>>(d_descs, d_cta0, n);
+      break;
+    case kRsWords32:
+      reshape_words_kernel<uint32_t><<<(unsigned)grid, 256, 0, s>>>(d_descs, d_cta0, n);
+      break;
+    case kRsWords64:
+      reshape_words_kernel<uint64_t><<<(unsigned)grid, 256, 0, s>>>(d_descs, d_cta0, n);
+      break;
+    default:
+      reshape_kernel<<<(unsigned)grid, 256, 0, s>>>(d_descs, d_cta0, n);
+      break;
   }
 }
 
-// Long rows (more than 16 words): one warp per (row, run of 256 words), lanes
-// on consecutive words; a row whose run meets a common bit sets its bit of the
-// pre-zeroed C atomically.
+// Long dot rows (more than 16 words) are split into runs of this many words.
 constexpr int64_t kDotRun = 256;
-__global__ void dot_wide_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
-                                unsigned long long* __restrict__ C, int64_t rows, int64_t M,
-                                int64_t Kw) {
+
+// ------------------------------------------- outer / dot / and, batched
+// Every such cluster of one tree level in one launch: job p owns blocks
+// [cta0[p], cta0[p+1]) and runs the loop of its kind over them.
+__global__ void __launch_bounds__(256)
+ewise_kernel(const EwJob* __restrict__ jobs, const int64_t* __restrict__ cta0, int n) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta0[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const EwJob& j = jobs[lo];
+  const int64_t bid = (int64_t)blockIdx.x - cta0[lo], nblk = cta0[lo + 1] - cta0[lo];
   const int lane = threadIdx.x & 31;
-  const int64_t nruns = (Kw + kDotRun - 1) / kDotRun;
-  const int64_t items = rows * nruns;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items;
-       it += nwarps) {
-    const int64_t r = it / nruns, w0 = (it - r * nruns) * kDotRun;
-    const int64_t w1 = min(Kw, w0 + kDotRun);
-    const uint64_t* a = A + r * Kw;
-    const uint64_t* b = B + (r / M) * Kw;
-    uint64_t acc = 0;
-    for (int64_t w = w0 + lane; w < w1; w += 32) acc |= a[w] & b[w];
-    if (__any_sync(0xffffffffu, acc != 0) && lane == 0) atomicOr(&C[r >> 6], 1ull << (r & 63));
+  const int64_t gwarp = bid * (blockDim.x >> 5) + (threadIdx.x >> 5), nwarps = nblk * (blockDim.x >> 5);
+  const uint64_t* __restrict__ A = j.a;
+  const uint64_t* __restrict__ B = j.b;
+  uint64_t* __restrict__ C = j.c;
+  if (j.kind == kEwAnd) {
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < j.rows; i += nblk * blockDim.x) C[i] = A[i] & B[i];
+  } else if (j.kind == kEwOuter) {
+    // C[r][w] = bit r of A ? B[r / M][w] : 0
+    const int64_t total = j.rows * j.nw;
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < total; i += nblk * blockDim.x) {
+      const int64_t r = i / j.nw, w = i - r * j.nw;
+      const uint64_t bit = (A[r >> 6] >> (r & 63)) & 1ull;
+      C[i] = bit ? B[(r / j.m) * j.nw + w] : 0ull;
+    }
+  } else if (j.kind == kEwDot) {
+    // one warp per word of C: lanes take bits r and r + 32
+    const int64_t words = (j.rows + 63) / 64;
+    for (int64_t cw = gwarp; cw < words; cw += nwarps) {
+      uint32_t half[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t r = cw * 64 + h * 32 + lane;
+        uint64_t acc = 0;
+        if (r < j.rows) {
+          const uint64_t* a = A + r * j.nw;
+          const uint64_t* b = B + (r / j.m) * j.nw;
+          for (int64_t w = 0; w < j.nw && !acc; ++w) acc = a[w] & b[w];
+        }
+        half[h] = __ballot_sync(0xffffffffu, acc != 0);
+      }
+      if (lane == 0) C[cw] = (uint64_t)half[0] | ((uint64_t)half[1] << 32);
+    }
+  } else {
+    // long rows: one warp per (row, run of 256 words) into the cleared C
+    const int64_t nruns = (j.nw + kDotRun - 1) / kDotRun;
+    const int64_t items = j.rows * nruns;
+    for (int64_t it = gwarp; it < items; it += nwarps) {
+      const int64_t r = it / nruns, w0 = (it - r * nruns) * kDotRun;
+      const int64_t w1 = min(j.nw, w0 + kDotRun);
+      const uint64_t* a = A + r * j.nw;
+      const uint64_t* b = B + (r / j.m) * j.nw;
+      uint64_t acc = 0;
+      for (int64_t w = w0 + lane; w < w1; w += 32) acc |= a[w] & b[w];
+      if (__any_sync(0xffffffffu, acc != 0) && lane == 0)
+        atomicOr(reinterpret_cast<unsigned long long*>(&C[r >> 6]), 1ull << (r & 63));
+    }
   }
 }
 
-void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
-                int64_t Kw, cudaStream_t s) {
-  const int64_t words = (rows + 63) / 64;
-  if (words <= 0) return;
-  if (Kw > 16) {
-    cudaMemsetAsync(C, 0, (size_t)words * 8, s);
-    const int64_t items = rows * ((Kw + kDotRun - 1) / kDotRun);
-    int64_t blocks = (items + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    dot_wide_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, reinterpret_cast<unsigned long long*>(C),
-                                                     rows, M, Kw);
-    return;
+int64_t ewise_blocks(const EwJob& j) {
+  int64_t items;
+  switch (j.kind) {
+    case kEwAnd: items = (j.rows + 255) / 256; break;
+    case kEwOuter: items = (j.rows * j.nw + 255) / 256; break;
+    case kEwDot: items = ((j.rows + 63) / 64 + 7) / 8; break;
+    default: items = (j.rows * ((j.nw + kDotRun - 1) / kDotRun) + 7) / 8; break;
   }
-  int64_t blocks = (words + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, C, rows, M, Kw);
+  return std::min<int64_t>(items, 152 * 16);
+}
+
+void launch_ewise(const EwJob* d_jobs, const int64_t* d_cta0, int n, int64_t grid, cudaStream_t s) {
+  if (n <= 0 || grid <= 0) return;
+  ewise_kernel<<<(unsigned)grid, 256, 0, s>>>(d_jobs, d_cta0, n);
 }
 
 // ---------------------------------------------------------------- row-OR
@@ -647,6 +685,20 @@ size_t table_bytes(int64_t staged, int Nt) { return (size_t)rowor_table_rows(sta
 
 EncodeTiledFn tensor_map_encoder() { return encode_fn(); }
 
+cudaError_t smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = set[{fn, dev}];
+  if (bytes <= have) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 void rowor_plan(RowOrDesc& d, int64_t target_ctas) {
   const bool tma_ok = (d.Nw % 2 == 0) && (reinterpret_cast<uintptr_t>(d.B) % 16 == 0) &&
                       (d.nbatch * d.K < (1ll << 31)) && encode_fn() != nullptr;
@@ -738,8 +790,7 @@ cudaError_t launch_rowor(const RowOrDesc* d_descs, const CUtensorMap* d_maps,
   cfg.numAttrs = 1;
 #define PA_ROWOR(GG)                                                                         \
   do {                                                                                       \
-    cudaFuncSetAttribute(rowor_tile_kernel<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)smem);                                                         \
+    smem_limit(reinterpret_cast<const void*>(rowor_tile_kernel<GG>), smem);                  \
     cudaLaunchKernelEx(&cfg, rowor_tile_kernel<GG>, d_descs, d_maps, d_cta0, nprob);         \
   } while (0)
   switch (Nt) {
@@ -772,20 +823,5 @@ void launch_popcount(const uint64_t* w, int64_t nwords, unsigned long long* out,
   popcount_kernel<<<(unsigned)blocks, 256, 0, s>>>(w, nwords, out);
 }
 
-// ------------------------------------------------------------------- AND
-__global__ void and_kernel(const uint64_t* __restrict__ a, const uint64_t* __restrict__ b,
-                           uint64_t* __restrict__ c, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    c[i] = a[i] & b[i];
-}
-
-void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords,
-                cudaStream_t s) {
-  if (nwords <= 0) return;
-  int64_t blocks = (nwords + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  and_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, b, c, nwords);
-}
 
 }  // namespace pa

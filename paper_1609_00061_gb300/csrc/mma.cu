@@ -553,7 +553,7 @@ cudaError_t launch_mma(const MmaDesc* d_descs, const CUtensorMap* d_maps, const 
                        int nprob, int64_t grid, cudaStream_t s) {
   if (nprob <= 0 || grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(mma_bool_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMmaSmem);
+  smem_limit(reinterpret_cast<const void*>(mma_bool_kernel), kMmaSmem);
   mma_bool_kernel<<<(unsigned)grid, kMmaThreads, kMmaSmem, s>>>(d_descs, d_maps, d_cta0, nprob);
   return cudaGetLastError();
 }

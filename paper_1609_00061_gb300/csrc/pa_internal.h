@@ -13,6 +13,11 @@
 
 namespace pa {
 
+// Raise kernel `fn`'s dynamic shared-memory limit on the current device only
+// when a launch needs more than any earlier one did (the attribute call costs
+// host time on every launch otherwise).  Thread-safe.
+cudaError_t smem_limit(const void* fn, size_t bytes);
+
 constexpr int kMaxDim = PA_MAX_DIM;
 constexpr int kMaxDeg = PA_MAX_DEGREE;
 
@@ -160,17 +165,33 @@ struct ReshapeDesc {
   int64_t t_in_L, t_out_J;           // input words per L step, output words per J step
   int64_t n_other;                   // transpose: product of u_res
 };
-void launch_reshape(const ReshapeDesc& d, cudaStream_t s);
+// Kernel variant of a reshape (kRs*) and its block count; a launch runs a
+// table of n descriptors of one kind, problem p on blocks [cta0[p], cta0[p+1])
+// (device arrays), grid = cta0[n].
+enum { kRsBits = 0, kRsWords32 = 1, kRsWords64 = 2, kRsTranspose = 3 };
+int reshape_kind(const ReshapeDesc& d);
+int64_t reshape_blocks(const ReshapeDesc& d);
+void launch_reshape(const ReshapeDesc* d_descs, const int64_t* d_cta0, int n, int kind,
+                    int64_t grid, cudaStream_t s);
 
-// Outer product of a K-free cluster: C row r (r = b * M + m) is B row b when bit
-// r of the flat bit vector A is set, else zero.  rows = nbatch * M.
-void launch_outer(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
-                  int64_t Nw, cudaStream_t s);
-// Cluster whose result keeps no axis of B alone: bit r (r = b * M + m) of the
-// flat bit vector C is set when row r of A and row b of B (Kw words each)
-// share a set bit.  rows = nbatch * M.
-void launch_dot(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t rows, int64_t M,
-                int64_t Kw, cudaStream_t s);
+// cudaSuccess when this build holds kernel code the current device can run
+cudaError_t probe_kernel_image();
+
+// Clusters that are not matrix products, batched like the contractions:
+// kEwOuter  C row r (r = b * M + m) is B row b (nw words) when bit r of A is set;
+// kEwDot    bit r of C = any(A row r AND B row r / M), rows of nw <= 16 words;
+// kEwDotWide the same for longer rows, OR-ed into a cleared C;
+// kEwAnd    C = A AND B over `rows` words.
+enum { kEwOuter = 0, kEwDot = 1, kEwDotWide = 2, kEwAnd = 3 };
+struct EwJob {
+  const uint64_t* a;
+  const uint64_t* b;
+  uint64_t* c;
+  int64_t rows, m, nw;
+  int32_t kind;
+};
+int64_t ewise_blocks(const EwJob& j);
+void launch_ewise(const EwJob* d_jobs, const int64_t* d_cta0, int n, int64_t grid, cudaStream_t s);
 
 // C[b*M + m, :] |= B[b*K + k, :] for every set bit k of A[b*M + m, :].
 // One CTA owns a tile of B (Kc rows x Nt words of batch b) in shared memory and
@@ -263,9 +284,6 @@ cudaError_t run_probe(int which, int sms, cudaStream_t s, double* per_s, double*
 void launch_random_bits(uint64_t* w, int64_t nwords, int64_t row_words, int64_t valid,
                         double density, uint64_t seed, cudaStream_t s);
 
-// cudaSuccess when this build holds kernel code the current device can run
-cudaError_t probe_kernel_image();
-void launch_and(const uint64_t* a, const uint64_t* b, uint64_t* c, int64_t nwords, cudaStream_t s);
 // *out += number of set bits in w[0..nwords) (padding bits are zero)
 void launch_popcount(const uint64_t* w, int64_t nwords, unsigned long long* out, cudaStream_t s);
 // One bounded mbarrier wait that nothing completes (sets *err after limit_ns).

@@ -493,8 +493,7 @@ void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_
   cfg.numAttrs = 1;
 #define PA_PLOT(DD)                                                                          \
   do {                                                                                       \
-    cudaFuncSetAttribute(plot_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                         (int)smem);                                                         \
+    smem_limit(reinterpret_cast<const void*>(plot_kernel<DD>), smem);                        \
     cudaLaunchKernelEx(&cfg, plot_kernel<DD>, d_jobs, njobs, ycap, gstride, rmax, d_zero,    \
                        nzero, zero_words);                                                   \
   } while (0)
