@@ -643,11 +643,14 @@ double or_density(double rho, double n);
 // Tensor-core path or row-OR for a matrix-form cluster?  Forced by
 // pa_set_contract_path, else the faster by the context's measured rates: the
 // row-OR is costed as (set bits of A) x (words per B row) word ORs at the rate
-// measured on random operands (runs of set bits make it faster than that,
-// so the estimate errs towards the tensor path), the tensor path
-// every multiply-add of its padded 128 x BN x 128 tiles (its rate includes
-// the expansion of both operands).  `ra` is A's estimated density (< 0:
-// unknown).
+// measured on random operands (runs of set bits make it faster than that)
+// plus a fixed cost per (row, K chunk, tile) unit; the tensor path as every
+// multiply-add of its padded 128 x BN x 128 tiles (its rate includes the
+// expansion of both operands; tile pairs it skips because one operand's tile
+// is empty are not credited, so the estimate errs towards the row-OR).  `ra`
+// is A's estimated density (< 0: unknown).
+constexpr double kRowOrUnitsPerUs = 3.0e3;
+
 bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   // no context (pa_solve_network_static): the row-OR, which needs no byte copies
   if (!ctx || ctx->path == PA_PATH_ROWOR || tensor_map_encoder() == nullptr) return false;
@@ -663,7 +666,19 @@ bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   // between the two measured points, constant outside them
   const double f = std::min(1.0, std::max(0.0, log(std::max(dens, 1e-12) / 0.02) / log(8.0)));
   const double rate_or = ctx->rate_or * pow(ctx->rate_or_dense / ctx->rate_or, f);
-  const double t_or = dens * M * K * nb * ceil(N / 64) / rate_or;
+  // every (row, K chunk, tile) unit of the row-OR also costs a fixed amount of
+  // bookkeeping: about 200 warp instructions (ncu, chain joins) at half the
+  // issue rate of 152 SMs x 4 schedulers x 2 GHz, some 3e9 units per second
+  RowOrDesc rd;
+  memset(&rd, 0, sizeof rd);
+  rd.nbatch = js.nbatch;
+  rd.M = js.M;
+  rd.K = js.K;
+  rd.Nw = (int64_t)ceil(N / 64);
+  rd.a_row_words = (js.K + 63) / 64;
+  rowor_plan(rd, 152);
+  const double units = nb * M * (double)rd.k_chunks * (double)rd.n_tiles;
+  const double t_or = dens * M * K * nb * ceil(N / 64) / rate_or + units / kRowOrUnitsPerUs;
   const double t_mma = macs / ctx->rate_mma;
   return t_mma < t_or;
 }
