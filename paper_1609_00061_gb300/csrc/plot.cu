@@ -378,51 +378,79 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int base = 0; base < nwords; base += blockDim.x) {
-    const int f = base + threadIdx.x;
-    bool keep = false;
-    if (f < nwords) {
-      keep = true;
-      const int r = f / row_words, w = f - r * row_words;
-      const int i0 = w * 64;
-      if (hoisted && res_last - i0 >= 64) {
-        float g[kG];
-        load_g(r, g);
-        const float4 th = thrs[r];
-        const float yc = ysmem ? ytab[i0 + w + 32] : __ldg(J->y32 + i0 + 32);
-        const float h = J->hword, ya = fabsf(yc), yw = ya + h;
-        // Horner for F and F' at y_c; S1 at |y_c| and S2 at |y_c| + h
-        float fc = g[D], dc = 0.0f, s1 = 0.0f, s2 = 0.0f;
-        for (int j = D - 1; j >= 0; --j) {
-          dc = __fmaf_rn(dc, yc, fc);
-          fc = __fmaf_rn(fc, yc, g[j]);
-        }
-        for (int j = D; j >= 1; --j) s1 = __fmaf_rn(s1, ya, (float)j * fabsf(g[j]));
-        for (int j = D; j >= 2; --j) s2 = __fmaf_rn(s2, yw, (float)(j * (j - 1)) * fabsf(g[j]));
-        const float e1 = (float)(2 * D + 4) * 5.9604645e-8f * s1;  // (2D + 4) 2^-24 S1
-        const float taylor = __fmaf_rn(h, fabsf(dc) + e1, 0.5f * h * h * s2) * 1.01f;
-        const float margin = __fmaf_rn(4.0f, th.z, taylor);
-        uint64_t* o = out + (row0 + r) * row_words + w;
-        if (kind == PA_EQ) {
-          if (fabsf(fc) > th.y + margin) {
-            *o = 0ull;
-            keep = false;
-          }
-        } else if (fc > th.y + margin) {
-          *o = 0ull;
-          keep = false;
-        } else if (fc < th.x - margin) {
-          *o = ~0ull;
-          keep = false;
+  // Taylor test of the pixels within h of y_c in row r: 1 when every one is
+  // certainly off, 2 when every one is certainly on, 0 when undecided
+  auto decide_span = [&](int r, float yc, float h) -> int {
+    float g[kG];
+    load_g(r, g);
+    const float4 th = thrs[r];
+    const float ya = fabsf(yc), yw = ya + h;
+    // Horner for F and F' at y_c; S1 at |y_c| and S2 at |y_c| + h
+    float fc = g[D], dc = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    for (int j = D - 1; j >= 0; --j) {
+      dc = __fmaf_rn(dc, yc, fc);
+      fc = __fmaf_rn(fc, yc, g[j]);
+    }
+    for (int j = D; j >= 1; --j) s1 = __fmaf_rn(s1, ya, (float)j * fabsf(g[j]));
+    for (int j = D; j >= 2; --j) s2 = __fmaf_rn(s2, yw, (float)(j * (j - 1)) * fabsf(g[j]));
+    const float e1 = (float)(2 * D + 4) * 5.9604645e-8f * s1;  // (2D + 4) 2^-24 S1
+    const float taylor = __fmaf_rn(h, fabsf(dc) + e1, 0.5f * h * h * s2) * 1.01f;
+    const float margin = __fmaf_rn(4.0f, th.z, taylor);
+    if (kind == PA_EQ) return (fabsf(fc) > th.y + margin) ? 1 : 0;
+    if (fc > th.y + margin) return 1;
+    if (fc < th.x - margin) return 2;
+    return 0;
+  };
+  // Spans of four full words are tested first (centre pixel 128, four times
+  // the word's half-width): on a sparse plot most of them are decided at once.
+  // Words of undecided spans (and of rows that are not whole spans) are
+  // tested one by one; the words no test decides go to phase 2.
+  const bool spans = hoisted && (row_words % 4 == 0) && (res_last == row_words * 64);
+  const int S = spans ? 4 : 1;
+  const int nspans = nwords / S;
+  for (int base = 0; base < nspans; base += blockDim.x) {
+    const int sp = base + threadIdx.x;
+    int span_dec = 0;  // this lane's span decided as a whole (1 off, 2 on)
+    int r = 0, w0 = 0;
+    if (sp < nspans) {
+      r = (sp * S) / row_words;
+      w0 = sp * S - r * row_words;
+      if (S == 4) {
+        const int i0 = w0 * 64;
+        const float yc = ysmem ? ytab[ypad(i0 + 128)] : __ldg(J->y32 + i0 + 128);
+        span_dec = decide_span(r, yc, 4.0f * J->hword);
+        if (span_dec) {
+          uint64_t* o = out + (row0 + r) * row_words + w0;
+          const uint64_t v = span_dec == 1 ? 0ull : ~0ull;
+          o[0] = v;
+          o[1] = v;
+          o[2] = v;
+          o[3] = v;
         }
       }
     }
-    // warp-aggregated append of the undecided words
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    int off = 0;
-    if (lane == 0 && m) off = atomicAdd(&s_n, __popc(m));
-    off = __shfl_sync(0xffffffffu, off, 0);
-    if (keep) list[off + __popc(m & ((1u << lane) - 1u))] = f;
+    for (int k = 0; k < S; ++k) {
+      bool keep = false;
+      if (sp < nspans && !span_dec) {
+        keep = true;
+        const int w = w0 + k;
+        const int i0 = w * 64;
+        if (hoisted && res_last - i0 >= 64) {
+          const float yc = ysmem ? ytab[i0 + w + 32] : __ldg(J->y32 + i0 + 32);
+          const int dec = decide_span(r, yc, J->hword);
+          if (dec) {
+            out[(row0 + r) * row_words + w] = dec == 1 ? 0ull : ~0ull;
+            keep = false;
+          }
+        }
+      }
+      // warp-aggregated append of the undecided words
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      int off = 0;
+      if (lane == 0 && m) off = atomicAdd(&s_n, __popc(m));
+      off = __shfl_sync(0xffffffffu, off, 0);
+      if (keep) list[off + __popc(m & ((1u << lane) - 1u))] = r * row_words + w0 + k;
+    }
   }
   __syncthreads();
   // Phase 2: pixel by pixel
