@@ -363,6 +363,10 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   const int kind = J->kind, strict = J->strict;
   const double eps = J->eps;
   uint64_t* __restrict__ out = J->out;
+  // read once: the stores to `out` below could otherwise make the compiler
+  // reload these from the job descriptor in every loop
+  const float hword = J->hword;
+  const float* __restrict__ y32 = J->y32;
   constexpr int kG = DS >= 0 ? DS + 1 : kMaxDeg + 1;
   const int nwords = nr * row_words;
   auto load_g = [&](int r, float* g) {
@@ -417,8 +421,8 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
       w0 = sp * S - r * row_words;
       if (S == 4) {
         const int i0 = w0 * 64;
-        const float yc = ysmem ? ytab[ypad(i0 + 128)] : __ldg(J->y32 + i0 + 128);
-        span_dec = decide_span(r, yc, 4.0f * J->hword);
+        const float yc = ysmem ? ytab[ypad(i0 + 128)] : __ldg(y32 + i0 + 128);
+        span_dec = decide_span(r, yc, 4.0f * hword);
         if (span_dec) {
           uint64_t* o = out + (row0 + r) * row_words + w0;
           const uint64_t v = span_dec == 1 ? 0ull : ~0ull;
@@ -436,8 +440,8 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
         const int w = w0 + k;
         const int i0 = w * 64;
         if (hoisted && res_last - i0 >= 64) {
-          const float yc = ysmem ? ytab[i0 + w + 32] : __ldg(J->y32 + i0 + 32);
-          const int dec = decide_span(r, yc, J->hword);
+          const float yc = ysmem ? ytab[i0 + w + 32] : __ldg(y32 + i0 + 32);
+          const int dec = decide_span(r, yc, hword);
           if (dec) {
             out[(row0 + r) * row_words + w] = dec == 1 ? 0ull : ~0ull;
             keep = false;
@@ -470,11 +474,11 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
       uint64_t pending = 0;
       const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
       if (kind == PA_EQ) {
-        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
-        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
       } else {
-        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
-        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, J->y32, i0, nb, &word, &pending);
+        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
       }
       while (pending) {
         const int bb = __ffsll((long long)pending) - 1;
