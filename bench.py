@@ -572,8 +572,12 @@ def run_ours(args, rank, world, local_rank):
         if profile:
             kern = pa.pa_profile_read(eng.ctx)
             pa.pa_profile_enable(eng.ctx, False)
-        return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, st, kern
+        per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        if not profile:
+            step_ms.extend(per_step)
+        return sum(per_step) / args.steps, st, kern
 
+    step_ms = []
     clocks = Clocks(dev)
     clocks.start()
     ms, st, _ = timed_steps(False)
@@ -623,6 +627,9 @@ def run_ours(args, rank, world, local_rank):
                    "contract_path": args.path, "tensor_core_joins": int(st["n_mma"]),
                    "autotuned_rates": rates,
                    "host_us_per_call": host_us,
+                   "step_ms_min_median_max": [min(step_ms), statistics.median(step_ms),
+                                              max(step_ms)],
+                   "step_ms_first": step_ms[:5],
                    "observed_join_densities": [round(float(x), 5) for x in observed]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(out.words.numel() * 8)},

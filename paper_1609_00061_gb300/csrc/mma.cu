@@ -135,42 +135,53 @@ __device__ __forceinline__ void transpose64(uint64_t& lo, uint64_t& hi, int lane
   }
 }
 
-// A operand: out[r][16 c .. 16 c + 15] = E4M3 bytes of bits 16 c .. 16 c + 15
-// of bit row r (zero past the row's words).  One thread per 16-byte chunk, so
-// a warp writes 512 contiguous bytes.
+// A operand: out[r][64 w .. 64 w + 63] = E4M3 bytes of word w of bit row r
+// (zero past the row's words).  One thread per input word; a warp's 32 words
+// are written as 128 16-byte chunks, four stores of 512 contiguous bytes each
+// (chunk c takes its 16 bits from the word of lane c / 4 by a shuffle).
 // Problem blockIdx.y of the table.
 __global__ void unpack_rows_kernel(const MmaDesc* __restrict__ descs) {
   const MmaDesc& d = descs[blockIdx.y];
   const uint64_t* __restrict__ in = d.A;
   uint8_t* __restrict__ out = d.Ab;
   const int64_t rows = d.nbatch * d.M, row_words = d.a_row_words, Kp = d.Kp;
-  const int64_t cpr = Kp / 16;
-  const int64_t total = rows * cpr;
-  // the loop's trip count is the same for every lane of a warp (total is
-  // rounded up to whole warps), so the occupancy ballot sees all 32 lanes
+  const int64_t wpr = Kp / 64;  // output words of 64 bytes per row (even)
+  const int64_t total = rows * wpr;
+  const int lane = threadIdx.x & 31;
+  // the trip count is the same for every lane of a warp (total rounded up to
+  // whole warps), so the shuffles and ballots see all 32 lanes
   const int64_t total_w = (total + 31) / 32 * 32;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_w;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t bits = 0;
-    int64_t r = 0, c = 0;
+    uint64_t word = 0;
+    int64_t r = 0, w = 0;
     if (i < total) {
-      r = i / cpr;
-      c = i - r * cpr;
-      const int64_t w = c >> 2;
-      const uint64_t word = w < row_words ? __ldg(in + r * row_words + w) : 0ull;
-      bits = (uint32_t)(word >> ((c & 3) * 16)) & 0xFFFFu;
-      reinterpret_cast<uint4*>(out)[i] = expand16(bits);
+      r = i / wpr;
+      w = i - r * wpr;
+      word = w < row_words ? __ldg(in + r * row_words + w) : 0ull;
     }
-    // one atomic per (row tile, K block) among the lanes whose chunk holds a
+    // chunk c = 32 j + lane of the warp's 128 is bits 16 (c % 4) .. of the
+    // word of lane c / 4; it lands at byte 16 c past the warp's first output
+    // byte, since the warp's words are consecutive in the output
+    const int64_t i0 = i - lane;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 32 * j + lane;
+      const uint64_t src = __shfl_sync(0xffffffffu, word, c >> 2);
+      if (i0 + (c >> 2) < total)
+        reinterpret_cast<uint4*>(out)[(i0 * 64 + 16 * (int64_t)c) / 16] =
+            expand16((uint32_t)(src >> ((c & 3) * 16)) & 0xFFFFu);
+    }
+    // one atomic per (row tile, K block) among the lanes whose word holds a
     // set bit: the lowest such lane of each tile and block sets its bit
     if (d.occ_a) {
-      const bool nzl = bits != 0;
+      const bool nzl = word != 0;
       const uint32_t nz = __ballot_sync(0xffffffffu, nzl);
       if (nzl) {
         const unsigned long long key =
-            (unsigned long long)(((r / d.M) * d.m_tiles + (r % d.M) / 128) * (Kp / 128) + c / 8);
+            (unsigned long long)(((r / d.M) * d.m_tiles + (r % d.M) / 128) * (Kp / 128) + w / 2);
         const uint32_t peers = __match_any_sync(nz, key);
-        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        if (lane == __ffs(peers) - 1) {
           const int64_t tile = (int64_t)key / (Kp / 128), kb = (int64_t)key % (Kp / 128);
           atomicOr(d.occ_a + tile * d.kb_words + kb / 32, 1u << (kb % 32));
         }
@@ -534,7 +545,7 @@ cudaError_t mma_encode_maps(const MmaDesc& d, CUtensorMap* maps2) {
 }
 
 int64_t unpack_blocks_a(const MmaDesc& d) {
-  return std::min<int64_t>((d.nbatch * d.M * (d.Kp / 16) + 255) / 256, 152 * 16);
+  return std::min<int64_t>((d.nbatch * d.M * (d.Kp / 64) + 255) / 256, 152 * 16);
 }
 
 int64_t unpack_blocks_b(const MmaDesc& d) {
