@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -651,6 +652,29 @@ double or_density(double rho, double n);
 // is A's estimated density (< 0: unknown).
 constexpr double kRowOrUnitsPerUs = 3.0e3;
 
+// Estimated microseconds of a matrix-form cluster on the row-OR path when A
+// has density `dens`: its word ORs at the context's measured rate (log-linear
+// in the density between the two measured points) plus every (row, K chunk,
+// tile) unit's fixed bookkeeping, about 200 warp instructions (ncu, chain
+// joins) at half the issue rate of 152 SMs x 4 schedulers x 2 GHz, some 3e9
+// units per second.
+double rowor_cost_us(const pa_ctx* ctx, const JoinShape& js, double dens) {
+  const double M = (double)js.M, N = js.nbits, K = (double)js.K, nb = (double)js.nbatch;
+  const double r0 = ctx ? ctx->rate_or : 2.0e5, r1 = ctx ? ctx->rate_or_dense : 9.0e5;
+  const double f = std::min(1.0, std::max(0.0, log(std::max(dens, 1e-12) / 0.02) / log(8.0)));
+  const double rate_or = r0 * pow(r1 / r0, f);
+  RowOrDesc rd;
+  memset(&rd, 0, sizeof rd);
+  rd.nbatch = js.nbatch;
+  rd.M = js.M;
+  rd.K = js.K;
+  rd.Nw = (int64_t)ceil(N / 64);
+  rd.a_row_words = (js.K + 63) / 64;
+  rowor_plan(rd, 152);
+  const double units = nb * M * (double)rd.k_chunks * (double)rd.n_tiles;
+  return dens * M * K * nb * ceil(N / 64) / rate_or + units / kRowOrUnitsPerUs;
+}
+
 bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   // no context (pa_solve_network_static): the row-OR, which needs no byte copies
   if (!ctx || ctx->path == PA_PATH_ROWOR || tensor_map_encoder() == nullptr) return false;
@@ -662,23 +686,7 @@ bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   const double macs = nb * ceil(M / 128) * 128 * ceil(N / BN) * BN * ceil(K / 128) * 128;
   if (macs < 134217728.0) return false;  // small clusters: the row-OR's launch is cheaper
   const double dens = ra >= 0 ? ra : 0.05;
-  // the row-OR rate grows with density (per-bit overheads amortise): log-linear
-  // between the two measured points, constant outside them
-  const double f = std::min(1.0, std::max(0.0, log(std::max(dens, 1e-12) / 0.02) / log(8.0)));
-  const double rate_or = ctx->rate_or * pow(ctx->rate_or_dense / ctx->rate_or, f);
-  // every (row, K chunk, tile) unit of the row-OR also costs a fixed amount of
-  // bookkeeping: about 200 warp instructions (ncu, chain joins) at half the
-  // issue rate of 152 SMs x 4 schedulers x 2 GHz, some 3e9 units per second
-  RowOrDesc rd;
-  memset(&rd, 0, sizeof rd);
-  rd.nbatch = js.nbatch;
-  rd.M = js.M;
-  rd.K = js.K;
-  rd.Nw = (int64_t)ceil(N / 64);
-  rd.a_row_words = (js.K + 63) / 64;
-  rowor_plan(rd, 152);
-  const double units = nb * M * (double)rd.k_chunks * (double)rd.n_tiles;
-  const double t_or = dens * M * K * nb * ceil(N / 64) / rate_or + units / kRowOrUnitsPerUs;
+  const double t_or = rowor_cost_us(ctx, js, dens);
   const double t_mma = macs / ctx->rate_mma;
   return t_mma < t_or;
 }
@@ -1373,7 +1381,36 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
     for (size_t k = 0; k < nets.size(); ++k)
       for (size_t t = 0; t < S[k].plan.joins.size(); ++t)
         n_in_level += (S[k].level[nets[k].nrel + t] == lv);
-    const int64_t target_ctas = std::max<int64_t>(1, 152 / std::max(1, n_in_level));
+    // The row-OR joins of a level share one launch; each gets a share of one
+    // wave of 152 CTAs in proportion to its estimated time, so a large join
+    // among many small ones is split over many CTAs instead of setting the
+    // launch's length alone.
+    std::map<std::pair<size_t, int>, int64_t> target_of;
+    {
+      std::vector<std::pair<std::pair<size_t, int>, double>> work;
+      double total = 0.0;
+      for (size_t k = 0; k < nets.size(); ++k) {
+        const State& s = S[k];
+        const int nrel = nets[k].nrel;
+        for (int t = 0; t < (int)s.plan.joins.size(); ++t) {
+          if (s.level[nrel + t] != lv) continue;
+          const Join& jn = s.plan.joins[t];
+          const JoinShape js = analyze_join(s.slots[jn.a], s.slots[jn.b], jn.keep, s.vres);
+          double w = 0.0;
+          if (!js.hadamard && !js.outer && !js.dot) {
+            double ra = 0.05;
+            if (!s.dens.empty() && s.dens[jn.a] >= 0 && s.dens[jn.b] >= 0)
+              ra = or_density(js.swap ? s.dens[jn.b] : s.dens[jn.a], js.private_a);
+            w = rowor_cost_us(bd.ctx, js, ra);
+          }
+          work.push_back({{k, t}, w});
+          total += w;
+        }
+      }
+      for (const auto& e : work)
+        target_of[e.first] =
+            total > 0 ? std::max<int64_t>(1, (int64_t)(152.0 * e.second / total)) : 1;
+    }
     bd.defer = !one_join_per_launch;
     for (size_t k = 0; k < nets.size(); ++k) {
       State& s = S[k];
@@ -1386,7 +1423,7 @@ void build_networks(Builder& bd, std::vector<Network>& nets, bool one_join_per_l
         const bool dn = !s.dens.empty();
         s.slots[nrel + t] = join(bd, s.slots[jn.a], s.slots[jn.b], jn.keep, s.vres,
                                  last ? &nets[k].target : nullptr,
-                                 one_join_per_launch ? 152 : target_ctas,
+                                 one_join_per_launch ? 152 : target_of[{k, t}],
                                  dn ? s.dens[jn.a] : -1.0, dn ? s.dens[jn.b] : -1.0,
                                  dn ? &s.dens[nrel + t] : nullptr);
         if (dn) {
