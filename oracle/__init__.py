@@ -16,6 +16,8 @@ Functions (passages of Spivak et al., arXiv 1609.00061):
   valid_tolerance   Sec. 3.2, Eq. (continuity): a valid tolerance for a polynomial
   plot              Sec. 3.2, sample-in-center plot
   eval_expr, plot_expr  expression relations (Sec. 2.1, Sec. 2.4) and their plot
+  plot_corner       the corner-lattice sample rule (an optional mode, not the
+                    paper's rule) with valid_tolerance(corner=True)
   gam               Sec. 3.3, Algorithm 1 (all arrays at once; tiny grids)
   contract          Sec. 3.3 Eq. (GAM) on one two-array cluster (Sec. 3.5)
   contract_count    the same cluster over the counting semiring (Sec. 2.2, footnote)
@@ -69,6 +71,13 @@ def _L():
         lib.or_eval_poly.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f64p]
         lib.or_valid_tolerance.restype = ctypes.c_double
         lib.or_valid_tolerance.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f64p, f64p, i32p]
+        lib.or_valid_tolerance_corner.restype = ctypes.c_double
+        lib.or_valid_tolerance_corner.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f64p, f64p,
+                                                  i32p]
+        lib.or_plot_corner.restype = ctypes.c_int
+        lib.or_plot_corner.argtypes = [ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int, f64p,
+                                       ctypes.c_int, i32p, f64p, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, f64p, f64p, i32p, u8p]
         lib.or_plot.restype = ctypes.c_int
         lib.or_plot.argtypes = [ctypes.c_int, ctypes.c_int, f64p, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_int, f64p, f64p, i32p, u8p]
@@ -143,12 +152,14 @@ class Arr:
     vars: tuple
 
 
-def valid_tolerance(degree: int, coeffs, lo, hi, res) -> float:
+def valid_tolerance(degree: int, coeffs, lo, hi, res, corner: bool = False) -> float:
+    """A valid tolerance for the centre rule, or (corner) for the corner rule."""
     c, cp = _f64(coeffs)
     l, lp = _f64(lo)
     h, hp = _f64(hi)
     r, rp = _i32(res)
-    return float(_L().or_valid_tolerance(len(r), degree, cp, lp, hp, rp))
+    fn = _L().or_valid_tolerance_corner if corner else _L().or_valid_tolerance
+    return float(fn(len(r), degree, cp, lp, hp, rp))
 
 
 def plot(degree: int, coeffs, kind: int, eps: float, lo, hi, res, strict: bool = False) -> np.ndarray:
@@ -190,23 +201,68 @@ def plot_expr(ops, consts, kind: int, eps: float, lo, hi, res, strict: bool = Fa
     return out
 
 
+RULE_CENTER, RULE_CORNER = 0, 1
+
+
+def plot_corner(port_var, nv, kind: int, eps: float, lo, hi, res, strict: bool = False,
+                degree: int = 0, coeffs=(), expr=None) -> np.ndarray:
+    """Corner-lattice plot over the nv distinct variables; port_var[p] is the
+    distinct variable port p reads.  A polynomial (degree, coeffs) or an
+    expression program expr = (ops, consts)."""
+    pv, pvp = _i32(port_var)
+    l, lp = _f64(lo)
+    h, hp = _f64(hi)
+    r, rp = _i32(res)
+    assert len(r) == nv
+    if expr is None:
+        c, cp = _f64(coeffs)
+        assert len(c) == coeff_count(len(pv), degree)
+        o, op = _i32([0])
+        k, kp = _f64([0.0])
+        nops = 0
+    else:
+        c, cp = _f64([0.0])
+        o, op = _i32(expr[0])
+        k, kp = _f64(expr[1] if len(expr[1]) else [0.0])
+        nops = len(o)
+    out = np.zeros(tuple(int(v) for v in r), dtype=np.uint8)
+    rc = _L().or_plot_corner(len(pv), pvp, nv, int(degree), cp, nops, op, kp, int(kind),
+                             float(eps), int(bool(strict)), lp, hp, rp, _u8(out))
+    assert rc == 0
+    return out
+
+
 def relation_eps(rel, axes) -> float:
-    """Tolerance of a relation: its own when given (>= 0), else a valid one."""
+    """Tolerance of a relation: its own when given (>= 0), else a valid one
+    for the relation's sample rule."""
     if rel.eps >= 0:
         return float(rel.eps)
     assert getattr(rel, "expr", None) is None, "expression relations carry their own eps"
     lo = [axes[v][0] for v in rel.vars]
     hi = [axes[v][1] for v in rel.vars]
     res = [axes[v][2] for v in rel.vars]
-    return valid_tolerance(rel.degree, rel.coeffs, lo, hi, res)
+    corner = getattr(rel, "rule", RULE_CENTER) == RULE_CORNER
+    return valid_tolerance(rel.degree, rel.coeffs, lo, hi, res, corner=corner)
 
 
 def plot_relation(rel, axes, strict: bool = False) -> Arr:
-    """Plot a relation over its ports (a repeated variable gives a repeated port)."""
+    """Plot a relation over its ports (a repeated variable gives a repeated
+    port); under the corner rule, over its distinct variables."""
     lo = [axes[v][0] for v in rel.vars]
     hi = [axes[v][1] for v in rel.vars]
     res = [axes[v][2] for v in rel.vars]
     eps = relation_eps(rel, axes)
+    if getattr(rel, "rule", RULE_CENTER) == RULE_CORNER:
+        dv = []
+        for v in rel.vars:
+            if v not in dv:
+                dv.append(v)
+        pv = [dv.index(v) for v in rel.vars]
+        data = plot_corner(pv, len(dv), rel.kind, eps, [axes[v][0] for v in dv],
+                           [axes[v][1] for v in dv], [axes[v][2] for v in dv], strict,
+                           degree=rel.degree, coeffs=rel.coeffs,
+                           expr=getattr(rel, "expr", None))
+        return Arr(data, tuple(dv))
     if getattr(rel, "expr", None) is not None:
         ops, consts = rel.expr
         return Arr(plot_expr(ops, consts, rel.kind, eps, lo, hi, res, strict), tuple(rel.vars))

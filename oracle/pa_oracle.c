@@ -20,6 +20,9 @@
  *                                        of the epsilon-tolerance sample-in-center plot
  *   or_eval_expr / or_plot_expr       -- expression relations (Sec. 2.1, Sec. 2.4) and
  *                                        their sample-in-center plot
+ *   or_plot_corner, or_valid_tolerance_corner
+ *                                     -- the corner-lattice sample rule (not the
+ *                                        paper's; an optional mode) and its tolerance
  *   or_gam                            -- Algorithm 1 (generalized array multiplication)
  *   or_contract_pair                  -- Eq. (GAM) for a two-array cluster (Sec. 3.5)
  *   or_contract_count                 -- the same cluster over the counting semiring
@@ -161,9 +164,11 @@ double or_eval_poly(int n, int degree, const double* coeffs, const double* x) {
  *   M_q = max(|lo_q|, |hi_q|),  delta_p = (hi_p - lo_p) / res_p.
  * The result is scaled by (1 + 2^-30) so that rounding in f(c) cannot turn a
  * pixel holding an exact solution off.  Fixed order: ports p ascending, monomials
- * in graded lex order, factors multiplied left to right as written above. */
-double or_valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
-                          const double* hi, const int* res) {
+ * in graded lex order, factors multiplied left to right as written above.
+ * `width` is the fraction of delta_p that a point of the pixel can lie from the
+ * sample point along port p: 1/2 for the centre, 1 for a corner (or_plot_corner). */
+static double tolerance(int n, int degree, const double* coeffs, const double* lo,
+                        const double* hi, const int* res, double width) {
   double M[OR_MAX_DIM];
   for (int q = 0; q < n; ++q) {
     double a = fabs(lo[q]), b = fabs(hi[q]);
@@ -195,9 +200,21 @@ double or_valid_tolerance(int n, int degree, const double* coeffs, const double*
       } while (n > 1 && next_tuple_desc(n, t, e));
     }
     double delta = (hi[p] - lo[p]) / (double)res[p];
-    total = total + Sp * (delta * 0.5);
+    total = total + Sp * (delta * width);
   }
   return total * (1.0 + 0x1p-30);
+}
+
+double or_valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
+                          const double* hi, const int* res) {
+  return tolerance(n, degree, coeffs, lo, hi, res, 0.5);
+}
+
+/* The same bound for the corner-lattice plot: every point of a pixel lies within
+ * delta_p of each of its corners along port p, so the full width is used. */
+double or_valid_tolerance_corner(int n, int degree, const double* coeffs, const double* lo,
+                                 const double* hi, const int* res) {
+  return tolerance(n, degree, coeffs, lo, hi, res, 1.0);
 }
 
 /* --------------------------------------------------------------------- plot
@@ -248,13 +265,6 @@ int or_plot(int n, int degree, const double* coeffs, int kind, double eps, int s
   return 0;
 }
 
-/* ------------------------------------------------------------- Algorithm 1
- * Generalized array multiplication for a wiring diagram with links
- * Lambda = {0..nlinks-1}: for every link entry e in Entr(Lambda), the product of
- * A_i(Entr^i(e)) over the inner packs is OR-ed into A'(Entr'(e)).  Port j of
- * array i is wired to link port_links[off_i + j]; the outer pack's ports are
- * wired to out_links.  Entr^i(e) reads the link value of every port.  Loops run
- * over every entry of Entr(Lambda) exactly as the algorithm states (tiny grids). */
 /* ------------------------------------------------------------- expressions
  * A relation given as an expression of its ports (the paper's examples in
  * Sec. 2.1 and Sec. 2.4 use |.|, cos, ln, tan, cosh, exp and reciprocals).
@@ -349,6 +359,71 @@ int or_plot_expr(int n, int nops, const int* ops, const double* consts, int kind
   return 0;
 }
 
+/* ---------------------------------------------------------- corner lattice
+ * An alternative sample rule, off by default (the paper's rule is the centre
+ * rule of or_plot): f is sampled on the lattice of grid corners.  Variable k has
+ * the res_k + 1 lattice coordinates lo_k + (double)i * delta_k, i = 0..res_k,
+ * delta_k = (hi_k - lo_k) / res_k (one product and one sum, each rounded), and
+ * pixel e has the 2^nv corners that take index e_k or e_k + 1 on each variable.
+ * Ports read variables through port_var (a variable on two ports reads one
+ * coordinate on both: the corners are those of the pixel over the distinct
+ * variables).  Pixel e is on iff some corner value c with finite f(c) achieves
+ * eps under the same comparison as or_plot, or, for kind 0, the finite corner
+ * values include one above 0 and one below 0 (f changes sign in the pixel).
+ * Corners with a non-finite value take part in neither test.  With
+ * eps >= or_valid_tolerance_corner every pixel holding a solution is on:
+ * |f(c) - f(x)| <= sum_p S_p * delta_p for any corner c of x's pixel.
+ * The relation is a polynomial (nops == 0: degree, coeffs) or an expression
+ * program (nops > 0: ops, consts, as in or_eval_expr).  lo, hi, res and the
+ * output axes are over the nv distinct variables, last variable fastest. */
+int or_plot_corner(int nports, const int* port_var, int nv, int degree, const double* coeffs,
+                   int nops, const int* ops, const double* consts, int kind, double eps,
+                   int strict, const double* lo, const double* hi, const int* res,
+                   uint8_t* out) {
+  if (nports < 1 || nports > OR_MAX_DIM || nv < 1 || nv > OR_MAX_DIM) return -1;
+  for (int p = 0; p < nports; ++p)
+    if (port_var[p] < 0 || port_var[p] >= nv) return -1;
+  int64_t total = 1;
+  for (int k = 0; k < nv; ++k) total *= res[k];
+  double delta[OR_MAX_DIM];
+  for (int k = 0; k < nv; ++k) delta[k] = (hi[k] - lo[k]) / (double)res[k];
+  int64_t* tab = nops > 0 ? NULL : build_index_table(nports, degree);
+#pragma omp parallel for schedule(static)
+  for (int64_t flat = 0; flat < total; ++flat) {
+    int64_t idx[OR_MAX_DIM];
+    int64_t rest = flat;
+    for (int k = nv - 1; k >= 0; --k) {
+      idx[k] = rest % res[k];
+      rest /= res[k];
+    }
+    int on = 0, pos = 0, neg = 0;
+    for (int m = 0; m < (1 << nv); ++m) {
+      double coord[OR_MAX_DIM], x[OR_MAX_DIM];
+      for (int k = 0; k < nv; ++k) {
+        int64_t i = idx[k] + ((m >> k) & 1);
+        coord[k] = lo[k] + (double)i * delta[k];
+      }
+      for (int p = 0; p < nports; ++p) x[p] = coord[port_var[p]];
+      double f = nops > 0 ? or_eval_expr(nops, ops, consts, x, NULL)
+                          : eval_with_table(nports, degree, coeffs, tab, x);
+      if (!isfinite(f)) continue;
+      if (decide(f, kind, eps, strict)) on = 1;
+      if (f > 0.0) pos = 1;
+      if (f < 0.0) neg = 1;
+    }
+    out[flat] = (uint8_t)(on || (kind == 0 && pos && neg));
+  }
+  free(tab);
+  return 0;
+}
+
+/* ------------------------------------------------------------- Algorithm 1
+ * Generalized array multiplication for a wiring diagram with links
+ * Lambda = {0..nlinks-1}: for every link entry e in Entr(Lambda), the product of
+ * A_i(Entr^i(e)) over the inner packs is OR-ed into A'(Entr'(e)).  Port j of
+ * array i is wired to link port_links[off_i + j]; the outer pack's ports are
+ * wired to out_links.  Entr^i(e) reads the link value of every port.  Loops run
+ * over every entry of Entr(Lambda) exactly as the algorithm states (tiny grids). */
 int or_gam(int nlinks, const int* link_res, int narr, const int* ndims,
            const int* port_links, const uint8_t* const* arrays, int nout,
            const int* out_links, uint8_t* out) {

@@ -23,6 +23,8 @@ from math import comb
 import numpy as np
 
 KIND_EQ, KIND_LE, KIND_LT = 0, 1, 2
+# Sample rules (include/pa.h, pa_rule): the paper's pixel centres, or the grid corners.
+RULE_CENTER, RULE_CORNER = 0, 1
 SEED_BASE = 0x160900061
 
 _M64 = (1 << 64) - 1
@@ -77,6 +79,7 @@ class Relation:
     kind: int = KIND_EQ
     eps: float = -1.0          # < 0: the solver derives a valid tolerance (polynomials)
     expr: tuple = None         # (int32 instructions, float64 constants) or None
+    rule: int = 0              # RULE_CENTER (the paper's) or RULE_CORNER
 
     def __post_init__(self):
         self.vars = tuple(int(v) for v in self.vars)
