@@ -126,6 +126,26 @@ typedef struct {
   const double* consts; /* HOST pointer: nconsts doubles */
 } pa_expr;
 
+/* ------------------------------------------------------------ sample rules
+ * PA_RULE_CENTER (default) is the paper's sample-in-center plot (above).
+ * PA_RULE_CORNER is an optional alternative that samples f on the lattice of
+ * grid corners instead: variable v has the res + 1 lattice coordinates
+ * lo + (double)i * delta, i = 0..res (one product and one sum, each rounded),
+ * and pixel e has the 2^d corners that take index e_v or e_v + 1 on each of
+ * the relation's d distinct variables (a variable on two ports reads the same
+ * coordinate on both).  The pixel is on when some corner c with finite f(c)
+ * passes the same comparison as the centre rule (|f(c)| <= eps for PA_EQ,
+ * f(c) <= eps for PA_LE, f(c) < eps for PA_LT, strict as above), or, for
+ * PA_EQ, when the finite corner values include one above 0 and one below 0 (a
+ * sign change inside the pixel).  Non-finite corner values take part in
+ * neither test; a value of exactly 0 has no sign.  The valid tolerance of this
+ * rule uses the full pixel width delta_p where the centre rule uses
+ * delta_p / 2 (pa_valid_tolerance), since every point of a pixel lies within
+ * delta_p of each of its corners along each axis.  Polynomial and expression
+ * relations both support it; the corner values are evaluated in the same
+ * IEEE double order as the centre values. */
+typedef enum { PA_RULE_CENTER = 0, PA_RULE_CORNER = 1 } pa_rule;
+
 /* A relation over `arity` ports; port p reads variable vars[p].  A variable
  * may fill several ports (a loop in the wiring diagram, Sec. 3.1): the
  * relation is then plotted on the diagonal.  With expr == NULL the relation is
@@ -133,7 +153,8 @@ typedef struct {
  * doubles in graded lex order.  With expr != NULL the relation is that
  * expression of the ports (degree and coeffs are ignored).  eps >= 0 is the
  * tolerance; eps < 0 asks the library for a valid one (pa_valid_tolerance;
- * polynomials only). */
+ * polynomials only).  rule is a pa_rule (0, the paper's centre rule, when the
+ * structure is zero-initialised). */
 typedef struct {
   int32_t arity;
   int32_t vars[PA_MAX_DIM];
@@ -142,6 +163,7 @@ typedef struct {
   int32_t kind;
   double eps;
   const pa_expr* expr;
+  int32_t rule;
 } pa_relation;
 
 /* A bit-packed Boolean array on the device (layout above).  `words` holds
@@ -297,14 +319,15 @@ int64_t pa_array_words(int32_t ndim, const int32_t* res);
  * (indexed by variable id), Sec. 3.2 Eq. (continuity): eps with
  * |f(x) - f(c)| <= eps whenever x lies in the pixel centred at c (an
  * expression relation returns PA_ERR_UNSUPPORTED).  Computed on the host as
- *   (1 + 2^-30) * sum_p S_p * delta_p / 2,
+ *   (1 + 2^-30) * sum_p S_p * delta_p / 2   (PA_RULE_CORNER: delta_p, c a corner),
  *   S_p = sum_e |c_e| e_p M_p^(e_p - 1) prod_{q != p} M_q^(e_q),  M_q = max(|lo_q|, |hi_q|),
  * in a fixed order (ports ascending, monomials in graded lex order, factors left
  * to right).  Host only, no GPU. */
 pa_status pa_valid_tolerance(const pa_relation* rel, const pa_axis* axes, int32_t nvars,
                              double* eps_out);
 
-/* Plot one relation (Sec. 3.2, sample-in-center plot) into `out`, whose vars
+/* Plot one relation (Sec. 3.2, sample-in-center plot, or the corner rule when
+ * rel->rule is PA_RULE_CORNER) into `out`, whose vars
  * must be the relation's distinct variables in order of first appearance and
  * whose res must match `axes`. */
 pa_status pa_plot(pa_ctx* ctx, const pa_relation* rel, const pa_axis* axes, int32_t nvars,

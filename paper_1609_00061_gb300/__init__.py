@@ -68,6 +68,7 @@ def _relations(rels):
         arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         arr[i].kind = int(r.kind)
         arr[i].eps = float(r.eps)
+        arr[i].rule = int(getattr(r, "rule", 0))
         ex = getattr(r, "expr", None)
         if ex is not None:
             ops = np.ascontiguousarray(ex[0], dtype=np.int32)
@@ -289,7 +290,7 @@ def _struct_dtype(ctype, fields):
 _AXIS_DT = _struct_dtype(PaAxis, [("lo", "<f8"), ("hi", "<f8"), ("res", "<i4")])
 _REL_DT = _struct_dtype(PaRelation, [("arity", "<i4"), ("vars", ("<i4", 8)), ("degree", "<i4"),
                                      ("coeffs", "<u8"), ("kind", "<i4"), ("eps", "<f8"),
-                                     ("expr", "<u8")])
+                                     ("expr", "<u8"), ("rule", "<i4")])
 _SYS_DT = _struct_dtype(PaSystem, [("nvars", "<i4"), ("axes", "<u8"), ("nrel", "<i4"),
                                    ("rels", "<u8"), ("nexposed", "<i4"), ("exposed", "<u8")])
 
@@ -327,6 +328,7 @@ def _systems(systems):
         rels["coeffs"][:m] = coeffs.ctypes.data + 8 * coff.astype(np.uint64)
         rels["kind"][:m] = [int(r.kind) for r in rels_all]
         rels["eps"][:m] = [float(r.eps) for r in rels_all]
+        rels["rule"][:m] = [int(getattr(r, "rule", 0)) for r in rels_all]
     keep = [axes, rels, coeffs]
     for i, r in enumerate(rels_all):
         ex = getattr(r, "expr", None)

@@ -29,7 +29,7 @@ def _nvcc() -> str:
 
 def _sources():
     return [os.path.join(_CSRC, f) for f in CU_SOURCES + CPP_SOURCES] + \
-        [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".h")] + \
+        [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".h", ".cuh"))] + \
         [os.path.join(INCLUDE, "pa.h")]
 
 
@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout + r.stderr)
 
     # an object is rebuilt when it is older than its source or any header
-    headers = max(os.path.getmtime(s) for s in srcs if s.endswith(".h"))
+    headers = max(os.path.getmtime(s) for s in srcs if s.endswith((".h", ".cuh")))
 
     def stale(job):
         obj, src = job[-1], job[-3]
@@ -94,7 +94,7 @@ class PaExpr(ctypes.Structure):
 class PaRelation(ctypes.Structure):
     _fields_ = [("arity", c_i32), ("vars", c_i32 * MAX_DIM), ("degree", c_i32),
                 ("coeffs", ctypes.POINTER(c_f64)), ("kind", c_i32), ("eps", c_f64),
-                ("expr", ctypes.POINTER(PaExpr))]
+                ("expr", ctypes.POINTER(PaExpr)), ("rule", c_i32)]
 
 
 class PaArray(ctypes.Structure):

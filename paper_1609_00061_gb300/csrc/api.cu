@@ -89,7 +89,7 @@ bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end()
 
 // ------------------------------------------------------------ program
 enum OpKind { OP_PLOT, OP_MEMSET, OP_RESHAPE, OP_ROWOR, OP_UNPACK,
-              OP_MMA, OP_CENTRES, OP_PLOT_EXPR, OP_PERMUTE, OP_EWISE };
+              OP_MMA, OP_CENTRES, OP_PLOT_EXPR, OP_PLOT_CORNER, OP_PERMUTE, OP_EWISE };
 
 struct Op {
   OpKind kind;
@@ -111,6 +111,7 @@ const char* op_name(const Op& op) {
     case OP_PLOT: return "plot_kernel";
     case OP_CENTRES: return "plot_centres_kernel";
     case OP_PLOT_EXPR: return "plot_expr_kernel";
+    case OP_PLOT_CORNER: return "plot_corner_kernel";
     case OP_PERMUTE: return "permute_u32_kernel";
     case OP_EWISE: return "ewise_kernel";
     case OP_MEMSET: return "memset";
@@ -933,6 +934,7 @@ void check_expr(pa_ctx* ctx, const pa_expr& e, int arity) {
 
 void check_relation(pa_ctx* ctx, const pa_relation& r, int32_t nvars) {
   PA_CHECK_ARG(r.arity >= 1 && r.arity <= PA_MAX_DIM, "relation arity must be in 1..8");
+  PA_CHECK_ARG(r.rule == PA_RULE_CENTER || r.rule == PA_RULE_CORNER, "relation rule");
   if (r.expr) {
     check_expr(ctx, *r.expr, r.arity);
     PA_CHECK_ARG(r.kind == PA_EQ || r.kind == PA_LE || r.kind == PA_LT, "relation kind");
@@ -968,7 +970,8 @@ double relation_eps(const pa_relation& r, const pa_axis* axes) {
     hi[p] = axes[r.vars[p]].hi;
     res[p] = axes[r.vars[p]].res;
   }
-  return valid_tolerance(r.arity, r.degree, r.coeffs, lo, hi, res);
+  return valid_tolerance(r.arity, r.degree, r.coeffs, lo, hi, res,
+                         r.rule == PA_RULE_CORNER ? 1.0 : 0.5);
 }
 
 void check_array(pa_ctx* ctx, const pa_array* a, const char* name) {
@@ -993,19 +996,95 @@ struct PlotReq {
 
 std::vector<BitArr> plot_poly(Builder& bd, const std::vector<PlotReq>& reqs);
 
-// Every requested plot: the expression relations in one launch (first, so
-// that the polynomial plot launch stays right before the contractions), the
-// polynomial ones in the two launches of plot_poly.  Arrays come back in the
-// order of `reqs`.
+// The relations plotted by the corner rule (pa.h, pa_rule), polynomial or
+// expression, in one launch; their arrays are appended to `plots` at `at`.
+void plot_corner(Builder& bd, const std::vector<PlotReq>& reqs, const std::vector<size_t>& at,
+                 std::vector<BitArr>& plots) {
+  std::vector<CornerJob> jobs;
+  std::vector<size_t> a_off, b_off;  // program and constants, or coefficients
+  int64_t words = 0;
+  for (size_t k = 0; k < reqs.size(); ++k) {
+    const pa_relation& r = *reqs[k].rel;
+    const pa_axis* axes = reqs[k].axes;
+    const std::vector<int> dv = distinct_vars(r);
+    BitArr a;
+    a.ndim = (int)dv.size();
+    a.inner = 1;
+    for (int d = 0; d < a.ndim; ++d) {
+      a.vars[d] = dv[d];
+      a.res[d] = axes[dv[d]].res;
+    }
+    a.w = reqs[k].direct ? reqs[k].direct : bd.alloc_words(a.words());
+    plots[at[k]] = a;
+    CornerJob J;
+    memset(&J, 0, sizeof J);
+    J.out = a.w;
+    J.arity = r.arity;
+    J.degree = r.degree;
+    J.kind = r.kind;
+    J.strict = reqs[k].strict;
+    J.eps = relation_eps(r, axes);
+    J.ndim = a.ndim;
+    for (int d = 0; d < a.ndim; ++d) J.res[d] = (int32_t)a.res[d];
+    for (int p = 0; p < r.arity; ++p) {
+      const pa_axis& ax = axes[r.vars[p]];
+      J.port_axis[p] = axis_of(a, r.vars[p]);
+      J.lo[p] = ax.lo;
+      J.delta[p] = (ax.hi - ax.lo) / (double)ax.res;
+    }
+    J.nrows = a.nrows();
+    J.row_words = a.row_words();
+    J.word0 = words;
+    words += a.words();
+    if (r.expr) {
+      J.nops = r.expr->nops;
+      a_off.push_back(bd.put(r.expr->ops, (size_t)r.expr->nops));
+      b_off.push_back(bd.put(r.expr->consts, (size_t)r.expr->nconsts));
+    } else {
+      std::vector<int64_t> ord = nest_order(r.arity, r.degree);
+      std::vector<double> nc(ord.size());
+      for (size_t c = 0; c < ord.size(); ++c) nc[c] = r.coeffs[ord[c]];
+      a_off.push_back(0);
+      b_off.push_back(bd.put(nc.data(), nc.size()));
+    }
+    jobs.push_back(J);
+    bd.st.pixels_plotted += (double)a.bits();
+    bd.st.n_plots++;
+  }
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    if (reqs[k].rel->expr) {
+      jobs[k].prog = reinterpret_cast<const int32_t*>(bd.dev(a_off[k]));
+      jobs[k].consts = reinterpret_cast<const double*>(bd.dev(b_off[k]));
+    } else {
+      jobs[k].coeffs = reinterpret_cast<const double*>(bd.dev(b_off[k]));
+    }
+  }
+  Op op;
+  op.kind = OP_PLOT_CORNER;
+  op.off0 = bd.put(jobs.data(), jobs.size(), 64);
+  op.n = (int)jobs.size();
+  op.count = words;
+  bd.ops.push_back(op);
+}
+
+// Every requested plot: the corner-rule relations and the expression relations
+// in one launch each (first, so that the polynomial plot launch stays right
+// before the contractions), the polynomial ones in the two launches of
+// plot_poly.  Arrays come back in the order of `reqs`.
 std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
   std::vector<BitArr> plots(reqs.size());
-  std::vector<PlotReq> poly;
-  std::vector<size_t> poly_at;
+  std::vector<PlotReq> poly, corner;
+  std::vector<size_t> poly_at, corner_at;
   std::vector<ExprJob> ejobs;
   std::vector<size_t> prog_off, const_off;
   int64_t words = 0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     const pa_relation& r = *reqs[i].rel;
+    if (r.rule == PA_RULE_CORNER) {
+      corner.push_back(reqs[i]);
+      corner_at.push_back(i);
+      continue;
+    }
     if (!r.expr) {
       poly.push_back(reqs[i]);
       poly_at.push_back(i);
@@ -1048,6 +1127,7 @@ std::vector<BitArr> plot_all(Builder& bd, const std::vector<PlotReq>& reqs) {
     bd.st.pixels_plotted += (double)a.bits();
     bd.st.n_plots++;
   }
+  if (!corner.empty()) plot_corner(bd, corner, corner_at, plots);
   if (!ejobs.empty()) {
     for (size_t k = 0; k < ejobs.size(); ++k) {
       ejobs[k].prog = reinterpret_cast<const int32_t*>(bd.dev(prog_off[k]));
@@ -1496,6 +1576,9 @@ void run_ops(pa_ctx* ctx, const std::vector<Op>& ops, char* blob, cudaStream_t s
       case OP_PLOT_EXPR:
         launch_plot_expr(reinterpret_cast<const ExprJob*>(blob + op.off0), op.n, op.count, s);
         break;
+      case OP_PLOT_CORNER:
+        launch_plot_corner(reinterpret_cast<const CornerJob*>(blob + op.off0), op.n, op.count, s);
+        break;
       case OP_CENTRES:
         launch_plot_centres(reinterpret_cast<const CentreTab*>(blob + op.off0), op.n, op.count, s);
         break;
@@ -1659,6 +1742,7 @@ std::vector<char> solve_key(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int
     put_val(k, r.degree);
     put_val(k, r.kind);
     put_val(k, r.eps);
+    put_val(k, r.rule);
     if (r.expr) {
       put_val(k, r.expr->nops);
       put_bytes(k, r.expr->ops, sizeof(int32_t) * r.expr->nops);
@@ -1952,7 +2036,7 @@ uint64_t relation_key(const pa_relation& r, const pa_axis* axes) {
     add(v);
   };
   add((uint64_t)r.arity << 32 | (uint32_t)r.degree);
-  add((uint64_t)r.kind);
+  add((uint64_t)r.kind | (uint64_t)(uint32_t)r.rule << 8);
   addd(r.eps);
   for (int p = 0; p < r.arity; ++p) {
     const pa_axis& a = axes[r.vars[p]];

@@ -79,6 +79,25 @@ struct ExprJob {
 // Every expression plot of a call in one launch, one thread per output word.
 void launch_plot_expr(const ExprJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s);
 
+// One relation plotted by the corner rule (pa.h, pa_rule): a polynomial
+// (prog == nullptr; coefficients in nest order) or an expression program.
+// lo and delta are per port; port_axis maps a port to its axis of `out`.
+struct CornerJob {
+  const int32_t* prog;
+  const double* consts;
+  const double* coeffs;
+  uint64_t* out;
+  double lo[kMaxDim];
+  double delta[kMaxDim];
+  double eps;
+  int64_t nrows, row_words, word0;
+  int32_t nops, degree, arity, kind, strict, ndim;
+  int32_t res[kMaxDim];
+  int32_t port_axis[kMaxDim];
+};
+// Every corner-rule plot of a call in one launch, one thread per output word.
+void launch_plot_corner(const CornerJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s);
+
 // A range of words to clear: words [w0, w0 + words) of the launch's flat
 // index space are p[0 .. words).
 struct ZeroRange {
@@ -293,7 +312,10 @@ cudaError_t launch_wait_selftest(int* err, long long limit_ns, cudaStream_t s);
 int64_t coeff_count(int n, int degree);
 // graded lex rank of every monomial in nest order (host)
 std::vector<int64_t> nest_order(int n, int degree);
+// A valid tolerance: (1 + 2^-30) sum_p S_p delta_p width, width = 1/2 for the
+// centre rule (a pixel's points lie within delta_p / 2 of its centre) and 1
+// for the corner rule.
 double valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
-                       const double* hi, const int32_t* res);
+                       const double* hi, const int32_t* res, double width);
 
 }  // namespace pa

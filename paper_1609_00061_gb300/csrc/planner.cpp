@@ -86,7 +86,7 @@ std::vector<int64_t> nest_order(int n, int degree) {
 }
 
 double valid_tolerance(int n, int degree, const double* coeffs, const double* lo,
-                       const double* hi, const int32_t* res) {
+                       const double* hi, const int32_t* res, double width) {
   std::vector<std::vector<int>> gl;
   graded_lex(n, degree, gl);
   double M[kMaxDim];
@@ -110,7 +110,7 @@ double valid_tolerance(int n, int degree, const double* coeffs, const double* lo
       S = S + t;
     }
     double delta = (hi[p] - lo[p]) / (double)res[p];
-    total = total + S * (delta * 0.5);
+    total = total + S * (delta * width);
   }
   return total * (1.0 + 0x1p-30);
 }

@@ -42,6 +42,7 @@
 
 #include <algorithm>
 
+#include "expr_eval.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -492,6 +493,90 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
     }
     out[row * row_words + w] = word;
   }
+}
+
+// ------------------------------------------------------- corner-rule plots
+// The corner rule of pa.h (pa_rule), one thread per output word.  For each of
+// the 2^(d-1) corner choices on the leading axes, f is evaluated at the lattice
+// points i0 .. i0 + nb of the last axis (65 for a full word); bit j of the
+// masks n / p / q records that lattice point j passes the comparison / has a
+// finite value above 0 / below 0.  Pixel b has lattice points b and b + 1 on
+// the last axis, so its bit in each pixel mask is m | m >> 1, with point 64
+// brought in at bit 63.  Off by default and evaluated in plain FP64 (no FP32
+// filter): every corner value costs one full evaluation.
+__device__ __forceinline__ double lattice_point(double lo, double delta, int64_t i) {
+  return __dadd_rn(lo, __dmul_rn((double)i, delta));
+}
+
+__global__ void __launch_bounds__(256)
+plot_corner_kernel(const CornerJob* __restrict__ jobs, int njobs, int64_t total_words) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total_words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].word0 <= w) lo = mid; else hi = mid - 1;
+    }
+    const CornerJob& J = jobs[lo];
+    const int64_t lw = w - J.word0;
+    const int64_t row = lw / J.row_words;
+    const int64_t wi = lw - row * J.row_words;
+    const int last = J.ndim - 1;
+    int64_t idx[kMaxDim];
+    int64_t rest = row;
+    for (int a = last - 1; a >= 0; --a) {
+      idx[a] = rest % J.res[a];
+      rest /= J.res[a];
+    }
+    const int i0 = (int)(wi * 64);
+    const int nb = min(64, J.res[last] - i0);
+    uint64_t near = 0, pos = 0, neg = 0;  // per pixel, OR over its corners
+    for (int m = 0; m < (1 << last); ++m) {
+      double x[kMaxDim];
+      for (int p = 0; p < J.arity; ++p) {
+        const int a = J.port_axis[p];
+        if (a != last) x[p] = lattice_point(J.lo[p], J.delta[p], idx[a] + ((m >> a) & 1));
+      }
+      uint64_t n = 0, pp = 0, q = 0;  // lattice points 0..63
+      uint64_t n64 = 0, p64 = 0, q64 = 0;  // lattice point 64
+      for (int j = 0; j <= nb; ++j) {
+        for (int p = 0; p < J.arity; ++p)
+          if (J.port_axis[p] == last) x[p] = lattice_point(J.lo[p], J.delta[p], i0 + j);
+        double f;
+        if (J.prog) {
+          f = run_expr(J.prog, J.nops, J.consts, x);
+        } else {
+          const double* cp = J.coeffs;
+          f = nest_rows(J.arity - 1, J.degree, cp, x);
+        }
+        const uint64_t cn = decide64(f, J.kind, J.eps, J.strict) ? 1ull : 0ull;
+        const uint64_t cpos = (isfinite(f) && f > 0.0) ? 1ull : 0ull;
+        const uint64_t cneg = (isfinite(f) && f < 0.0) ? 1ull : 0ull;
+        if (j < 64) {
+          n |= cn << j;
+          pp |= cpos << j;
+          q |= cneg << j;
+        } else {
+          n64 = cn;
+          p64 = cpos;
+          q64 = cneg;
+        }
+      }
+      near |= n | (n >> 1) | (n64 << 63);
+      pos |= pp | (pp >> 1) | (p64 << 63);
+      neg |= q | (q >> 1) | (q64 << 63);
+    }
+    uint64_t word = near | (J.kind == PA_EQ ? (pos & neg) : 0ull);
+    if (nb < 64) word &= (1ull << nb) - 1ull;
+    J.out[lw] = word;
+  }
+}
+
+void launch_plot_corner(const CornerJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s) {
+  if (njobs <= 0 || total_words <= 0) return;
+  int64_t blocks = (total_words + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  plot_corner_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total_words);
 }
 
 cudaError_t probe_kernel_image() {

@@ -63,10 +63,24 @@ def test_tolerance_matches_oracle_bitwise(orc):
             a, b = sorted(-5 + 10 * rng.uniform(2))
             axes.append((a, b + 0.01, int(rng.integers(2, 3000, 1)[0])))
         vars_ = [int(v) for v in rng.integers(0, nv - 1, arity)]
-        rel = W.Relation(vars_, degree, rng.normal(W.coeff_count(arity, degree)))
+        rule = trial % 2
+        rel = W.Relation(vars_, degree, rng.normal(W.coeff_count(arity, degree)), rule=rule)
         got = pa.pa_valid_tolerance(rel, axes)
         want = orc.relation_eps(rel, axes)
         assert got == want, (trial, got, want)
+
+
+def test_corner_rule_arguments():
+    """The corner rule's tolerance is twice the centre rule's (full pixel
+    width); a rule outside pa_rule is rejected before any GPU work."""
+    axes = [(-2.0, 2.0, 64), (-1.0, 3.0, 48)]
+    c = np.array([0.5, 1.0, -2.0, 0.25, 0.0, 1.5])
+    e0 = pa.pa_valid_tolerance(W.Relation((0, 1), 2, c), axes)
+    e1 = pa.pa_valid_tolerance(W.Relation((0, 1), 2, c, rule=W.RULE_CORNER), axes)
+    assert e1 == 2.0 * e0 > 0
+    with pytest.raises(pa.PaError) as e:
+        pa.pa_valid_tolerance(W.Relation((0, 1), 2, c, rule=2), axes)
+    assert e.value.status == 1
 
 
 def test_tree_cost_paper_example(lib):
