@@ -2,10 +2,12 @@
 // relations built from the ports with arithmetic and elementary functions,
 // as in the examples of Sec. 2.1 and Sec. 2.4).
 //
-// One thread per output word: the 64 pixels of the word are evaluated one
-// after the other, each by running the relation's postfix program over a
-// small stack in FP64.  The pixel centre is computed as for polynomial
-// relations, lo + ((double)i + 0.5) * delta with two IEEE roundings.
+// One thread per pixel, each running the relation's postfix program over a
+// small stack in FP64; a warp covers half an output word.  The pixel centre is
+// computed as for polynomial relations, lo + ((double)i + 0.5) * delta with
+// two IEEE roundings.  (With one thread per 64-pixel word, the paper's
+// examples at 125 x 125 pixels gave a few hundred threads, and the FP64
+// elementary functions ran one pixel after another on a few SMs.)
 #include <math.h>
 
 #include "expr_eval.cuh"
@@ -18,10 +20,18 @@ __device__ __forceinline__ double expr_centre(double lo, double delta, int64_t i
   return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), delta));
 }
 
+// One warp per 32-pixel half of an output word, one lane per pixel; the
+// ballot of the lanes' decisions is the half's 32 bits, stored as one 32-bit
+// word (the low half of a little-endian uint64 holds pixels 0..31).  Every
+// lane of a warp runs the same program, so the lanes stay converged.
 __global__ void __launch_bounds__(256)
-plot_expr_kernel(const ExprJob* __restrict__ jobs, int njobs, int64_t total_words) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total_words;
-       w += (int64_t)gridDim.x * blockDim.x) {
+plot_expr_kernel(const ExprJob* __restrict__ jobs, int njobs, int64_t total_halves) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t hw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       hw < total_halves; hw += nwarps) {
+    const int64_t w = hw >> 1;
+    const int half = (int)(hw & 1);
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -38,24 +48,23 @@ plot_expr_kernel(const ExprJob* __restrict__ jobs, int njobs, int64_t total_word
       rest /= J.res[a];
     }
     const int res_last = J.res[J.ndim - 1];
-    const int i0 = (int)(wi * 64);
-    const int nb = min(64, res_last - i0);
-    double x[kMaxDim];
-    for (int p = 0; p < J.arity; ++p)
-      if (J.port_axis[p] != J.ndim - 1) x[p] = expr_centre(J.lo[p], J.delta[p], idx[J.port_axis[p]]);
-    uint64_t word = 0;
-    for (int b = 0; b < nb; ++b) {
-      for (int p = 0; p < J.arity; ++p)
-        if (J.port_axis[p] == J.ndim - 1) x[p] = expr_centre(J.lo[p], J.delta[p], i0 + b);
+    const int b = half * 32 + lane;             // bit of the word
+    const int i = (int)(wi * 64) + b;            // pixel on the last axis
+    bool on = false;
+    if (i < res_last) {
+      double x[kMaxDim];
+      for (int p = 0; p < J.arity; ++p) {
+        const int a = J.port_axis[p];
+        x[p] = expr_centre(J.lo[p], J.delta[p], a == J.ndim - 1 ? (int64_t)i : idx[a]);
+      }
       const double f = run_expr(J.prog, J.nops, J.consts, x);
-      bool on = false;
       if (isfinite(f)) {
         const double d = (J.kind == PA_EQ) ? fabs(f) : f;
         on = (J.strict || J.kind == PA_LT) ? (d < J.eps) : (d <= J.eps);
       }
-      if (on) word |= 1ull << b;
     }
-    J.out[lw] = word;
+    const uint32_t bits = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) reinterpret_cast<uint32_t*>(J.out + lw)[half] = bits;
   }
 }
 
@@ -63,9 +72,10 @@ plot_expr_kernel(const ExprJob* __restrict__ jobs, int njobs, int64_t total_word
 
 void launch_plot_expr(const ExprJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s) {
   if (njobs <= 0 || total_words <= 0) return;
-  int64_t blocks = (total_words + 255) / 256;
+  const int64_t halves = 2 * total_words;
+  int64_t blocks = (halves + 7) / 8;  // 8 warps per block
   if (blocks > 152 * 16) blocks = 152 * 16;
-  plot_expr_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total_words);
+  plot_expr_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, halves);
 }
 
 }  // namespace pa

@@ -76,7 +76,8 @@ struct ExprJob {
   int32_t res[kMaxDim];
   int32_t port_axis[kMaxDim];
 };
-// Every expression plot of a call in one launch, one thread per output word.
+// Every expression plot of a call in one launch, one thread per pixel (a
+// warp per 32-pixel half of an output word).
 void launch_plot_expr(const ExprJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s);
 
 // One relation plotted by the corner rule (pa.h, pa_rule): a polynomial
@@ -95,7 +96,7 @@ struct CornerJob {
   int32_t res[kMaxDim];
   int32_t port_axis[kMaxDim];
 };
-// Every corner-rule plot of a call in one launch, one thread per output word.
+// Every corner-rule plot of a call in one launch, one thread per output byte.
 void launch_plot_corner(const CornerJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s);
 
 // A range of words to clear: words [w0, w0 + words) of the launch's flat

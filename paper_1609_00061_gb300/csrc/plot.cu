@@ -496,22 +496,25 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
 }
 
 // ------------------------------------------------------- corner-rule plots
-// The corner rule of pa.h (pa_rule), one thread per output word.  For each of
-// the 2^(d-1) corner choices on the leading axes, f is evaluated at the lattice
-// points i0 .. i0 + nb of the last axis (65 for a full word); bit j of the
-// masks n / p / q records that lattice point j passes the comparison / has a
-// finite value above 0 / below 0.  Pixel b has lattice points b and b + 1 on
-// the last axis, so its bit in each pixel mask is m | m >> 1, with point 64
-// brought in at bit 63.  Off by default and evaluated in plain FP64 (no FP32
-// filter): every corner value costs one full evaluation.
+// The corner rule of pa.h (pa_rule), one thread per output byte (8 pixels of
+// the last axis).  For each of the 2^(d-1) corner choices on the leading axes,
+// f is evaluated at the lattice points i0 .. i0 + nb of the last axis (9 for a
+// full byte); bit j of the masks n / p / q records that lattice point j passes
+// the comparison / has a finite value above 0 / below 0.  Pixel b has lattice
+// points b and b + 1 on the last axis, so its bit in each pixel mask is
+// m | m >> 1.  Bytes past the last pixel of a row are written as 0.  Off by
+// default and evaluated in plain FP64 (no FP32 filter): every corner value
+// costs one full evaluation, 9/8 per pixel and leading corner choice.
 __device__ __forceinline__ double lattice_point(double lo, double delta, int64_t i) {
   return __dadd_rn(lo, __dmul_rn((double)i, delta));
 }
 
 __global__ void __launch_bounds__(256)
-plot_corner_kernel(const CornerJob* __restrict__ jobs, int njobs, int64_t total_words) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total_words;
-       w += (int64_t)gridDim.x * blockDim.x) {
+plot_corner_kernel(const CornerJob* __restrict__ jobs, int njobs, int64_t total_bytes) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total_bytes;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = t >> 3;
+    const int byte = (int)(t & 7);
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -528,17 +531,16 @@ plot_corner_kernel(const CornerJob* __restrict__ jobs, int njobs, int64_t total_
       idx[a] = rest % J.res[a];
       rest /= J.res[a];
     }
-    const int i0 = (int)(wi * 64);
-    const int nb = min(64, J.res[last] - i0);
-    uint64_t near = 0, pos = 0, neg = 0;  // per pixel, OR over its corners
-    for (int m = 0; m < (1 << last); ++m) {
+    const int i0 = (int)(wi * 64) + 8 * byte;
+    const int nb = min(8, J.res[last] - i0);  // pixels of this byte (<= 0: padding)
+    uint32_t near = 0, pos = 0, neg = 0;  // per pixel, OR over its corners
+    for (int m = 0; nb > 0 && m < (1 << last); ++m) {
       double x[kMaxDim];
       for (int p = 0; p < J.arity; ++p) {
         const int a = J.port_axis[p];
         if (a != last) x[p] = lattice_point(J.lo[p], J.delta[p], idx[a] + ((m >> a) & 1));
       }
-      uint64_t n = 0, pp = 0, q = 0;  // lattice points 0..63
-      uint64_t n64 = 0, p64 = 0, q64 = 0;  // lattice point 64
+      uint32_t n = 0, pp = 0, q = 0;  // lattice points 0..nb
       for (int j = 0; j <= nb; ++j) {
         for (int p = 0; p < J.arity; ++p)
           if (J.port_axis[p] == last) x[p] = lattice_point(J.lo[p], J.delta[p], i0 + j);
@@ -549,34 +551,26 @@ plot_corner_kernel(const CornerJob* __restrict__ jobs, int njobs, int64_t total_
           const double* cp = J.coeffs;
           f = nest_rows(J.arity - 1, J.degree, cp, x);
         }
-        const uint64_t cn = decide64(f, J.kind, J.eps, J.strict) ? 1ull : 0ull;
-        const uint64_t cpos = (isfinite(f) && f > 0.0) ? 1ull : 0ull;
-        const uint64_t cneg = (isfinite(f) && f < 0.0) ? 1ull : 0ull;
-        if (j < 64) {
-          n |= cn << j;
-          pp |= cpos << j;
-          q |= cneg << j;
-        } else {
-          n64 = cn;
-          p64 = cpos;
-          q64 = cneg;
-        }
+        n |= (decide64(f, J.kind, J.eps, J.strict) ? 1u : 0u) << j;
+        pp |= ((isfinite(f) && f > 0.0) ? 1u : 0u) << j;
+        q |= ((isfinite(f) && f < 0.0) ? 1u : 0u) << j;
       }
-      near |= n | (n >> 1) | (n64 << 63);
-      pos |= pp | (pp >> 1) | (p64 << 63);
-      neg |= q | (q >> 1) | (q64 << 63);
+      near |= n | (n >> 1);
+      pos |= pp | (pp >> 1);
+      neg |= q | (q >> 1);
     }
-    uint64_t word = near | (J.kind == PA_EQ ? (pos & neg) : 0ull);
-    if (nb < 64) word &= (1ull << nb) - 1ull;
-    J.out[lw] = word;
+    uint32_t bits = near | (J.kind == PA_EQ ? (pos & neg) : 0u);
+    bits = nb > 0 ? bits & ((1u << nb) - 1u) : 0u;
+    reinterpret_cast<uint8_t*>(J.out + lw)[byte] = (uint8_t)bits;
   }
 }
 
 void launch_plot_corner(const CornerJob* d_jobs, int njobs, int64_t total_words, cudaStream_t s) {
   if (njobs <= 0 || total_words <= 0) return;
-  int64_t blocks = (total_words + 255) / 256;
+  const int64_t bytes = 8 * total_words;
+  int64_t blocks = (bytes + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  plot_corner_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, total_words);
+  plot_corner_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, bytes);
 }
 
 cudaError_t probe_kernel_image() {
