@@ -172,18 +172,22 @@ __global__ void unpack_rows_kernel(const MmaDesc* __restrict__ descs) {
         reinterpret_cast<uint4*>(out)[(i0 * 64 + 16 * (int64_t)c) / 16] =
             expand16((uint32_t)(src >> ((c & 3) * 16)) & 0xFFFFu);
     }
-    // one atomic per (row tile, K block) among the lanes whose word holds a
-    // set bit: the lowest such lane of each tile and block sets its bit
+    // occupancy: the lanes whose word holds a set bit OR their (row tile,
+    // K block) bits together per bitmap word, and one lane per word issues
+    // the atomic (a warp covering one row of K <= 4096 issues one), skipped
+    // when the bits are already set: every row of a tile sets the same bits,
+    // and same-address atomics queue at L2
     if (d.occ_a) {
       const bool nzl = word != 0;
       const uint32_t nz = __ballot_sync(0xffffffffu, nzl);
       if (nzl) {
-        const unsigned long long key =
-            (unsigned long long)(((r / d.M) * d.m_tiles + (r % d.M) / 128) * (Kp / 128) + w / 2);
-        const uint32_t peers = __match_any_sync(nz, key);
+        const int64_t tile = (r / d.M) * d.m_tiles + (r % d.M) / 128, kb = w / 2;
+        const int64_t widx = tile * d.kb_words + kb / 32;
+        const uint32_t peers = __match_any_sync(nz, (unsigned long long)widx);
+        const uint32_t bits = __reduce_or_sync(peers, 1u << (kb % 32));
         if (lane == __ffs(peers) - 1) {
-          const int64_t tile = (int64_t)key / (Kp / 128), kb = (int64_t)key % (Kp / 128);
-          atomicOr(d.occ_a + tile * d.kb_words + kb / 32, 1u << (kb % 32));
+          uint32_t* o = d.occ_a + widx;
+          if ((__ldcg(o) & bits) != bits) atomicOr(o, bits);
         }
       }
     }
@@ -198,6 +202,9 @@ __global__ void unpack_rows_kernel(const MmaDesc* __restrict__ descs) {
 // K rows >= K give zeros.
 // Problem blockIdx.y of the table.
 __global__ void unpack_transpose_kernel(const MmaDesc* __restrict__ descs) {
+  // the contraction launch that follows may start its set-up now; it waits
+  // for this grid to finish before it reads anything written here
+  asm volatile("griddepcontrol.launch_dependents;");
   const MmaDesc& d = descs[blockIdx.y];
   const uint64_t* __restrict__ in = d.B;
   uint8_t* __restrict__ out = d.Bb;
@@ -217,7 +224,9 @@ __global__ void unpack_transpose_kernel(const MmaDesc* __restrict__ descs) {
     // a 64 x 64 block lies inside one (column tile, K block) pair
     if (d.occ_b && __any_sync(0xffffffffu, (lo | hi) != 0ull) && lane == 0) {
       const int64_t nt = (nbk * 64) / d.BN, kblock = (kb * 64) / 128;
-      atomicOr(d.occ_b + (b * d.n_tiles + nt) * d.kb_words + kblock / 32, 1u << (kblock % 32));
+      uint32_t* o = d.occ_b + (b * d.n_tiles + nt) * d.kb_words + kblock / 32;
+      const uint32_t bit = 1u << (kblock % 32);
+      if (!(__ldcg(o) & bit)) atomicOr(o, bit);
     }
     transpose64(lo, hi, lane);
     uint8_t* dst = out + (b * N) * Kp + kb * 64;
@@ -237,6 +246,14 @@ __global__ void unpack_transpose_kernel(const MmaDesc* __restrict__ descs) {
 // One CTA per (problem, batch, 128-row tile of A, BN-column tile of B).
 // Warp 0 lane 0: TMA producer.  Warp 1 lane 0: MMA issuer.  Warp 2: TMEM
 // allocation.  Warps 4-7: epilogue (warp 4 + j reads TMEM lanes 32j..32j+31).
+//
+// Start-up: the launch may begin while the expansion kernel that writes the
+// operands and occupancy bitmaps is still running (programmatic dependent
+// launch).  Thread 0 reads the descriptor, initialises the barriers and
+// signals the other warps through a named barrier, then waits for the
+// expansion to finish (griddepcontrol.wait) and issues its first copies at
+// once, while warp 2 allocates TMEM; no role reads the operands, the bitmaps
+// or C before its own griddepcontrol.wait.
 __global__ void __launch_bounds__(kMmaThreads, 1)
 mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict__ maps,
                 const int64_t* __restrict__ cta0s, int nprob) {
@@ -247,39 +264,46 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
   uint64_t* empty = full + kMmaStages;
   uint64_t* accum = empty + kMmaStages;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accum + 1);
-  int* sfail = reinterpret_cast<int*>(tslot + 1);
-  int* sp = sfail + 1;
+  volatile int* sfail = reinterpret_cast<volatile int*>(tslot + 1);
+  int* sp = const_cast<int*>(sfail) + 1;
   __shared__ MmaDesc sd;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t tmem = 0;  // warps 1-7 (the producer never touches TMEM)
 
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = nprob - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (cta0s[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  if (warp == 0) {
+    if (lane == 0) {
+      int lo = 0, hi = nprob - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cta0s[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+      }
+      *sp = lo;
+      sd = descs[lo];
+      for (int s = 0; s < kMmaStages; ++s) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])) : "memory");
+      }
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(accum)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      *sfail = 0;
     }
-    *sp = lo;
-    sd = descs[lo];
-    for (int s = 0; s < kMmaStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&empty[s])) : "memory");
+    __syncwarp();
+    // descriptor, barriers and failure word are ready for warps 1-7
+    asm volatile("bar.arrive 1, %0;" ::"r"(kMmaThreads) : "memory");
+  } else {
+    if (warp == 2) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_addr(tslot)),
+                   "r"(kMmaTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(accum)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    *sfail = 0;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(kMmaThreads) : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = *tslot;
   }
-  if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(tslot)),
-                 "r"(kMmaTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
   const int p = *sp;
   const MmaDesc& d = sd;
   int64_t t = (int64_t)blockIdx.x - cta0s[p];
@@ -298,12 +322,15 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
   const int kbw = (nk + 31) / 32;
   auto active = [&](int w) -> uint32_t {
     uint32_t m = 0xffffffffu;
-    if (occa) m &= __ldg(occa + w);
-    if (occb) m &= __ldg(occb + w);
+    if (occa) m &= __ldcg(occa + w);
+    if (occb) m &= __ldcg(occb + w);
     if (w == kbw - 1 && (nk & 31)) m &= (1u << (nk & 31)) - 1u;
     return m;
   };
 
+  // the operands, the bitmaps and C belong to the expansion kernel until it
+  // has finished: each role waits for it (griddepcontrol.wait) right before
+  // its first access to them
   if (warp == 0) {
     if (lane == 0) {
       const CUtensorMap* ma = maps + 2 * p;
@@ -311,6 +338,7 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
       // the tensor maps were written to global memory by a copy before the launch
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma) : "memory");
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb) : "memory");
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       int j = 0;
       bool failed = false;
       for (int w = 0; w < kbw && !failed; ++w) {
@@ -344,10 +372,16 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
           ++j;
         }
       }
+      // after a failure anywhere, wait (bounded) for the copies still in
+      // flight before the CTA's shared memory is released
+      if (*sfail)
+        for (int q = j > kMmaStages ? j - kMmaStages : 0; q < j; ++q)
+          bar_wait(&full[q % kMmaStages], (uint32_t)(q / kMmaStages) & 1u);
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       const uint32_t idesc = f8_idesc(kMmaBM, BN);
       int j = 0;
       bool failed = false;
@@ -388,54 +422,70 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
     __syncwarp();
   } else if (warp >= 4) {
     const int ew = warp - 4;
-    const bool ok = bar_wait(accum, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // no K block in common: nothing was accumulated, every sum is zero
+    // (decided while the products run)
     bool none = true;
     for (int w = 0; w < kbw && none; ++w) none = (active(w) == 0);
+    const bool ok = bar_wait(accum, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool store = ok && !*sfail;
     const int64_t m = mt * kMmaBM + ew * 32 + lane;
-    for (int c = 0; c < BN / 64; ++c) {
-      uint32_t v[64];
-      const uint32_t ta = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(c * 64);
+    // up to 128 columns per round: every TMEM load of the round is in flight
+    // before the one wait
+    const int G = BN < 128 ? BN : 128;
+    for (int c0 = 0; c0 < BN; c0 += G) {
+      uint32_t v[128];
+      const uint32_t ta = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0;
       if (none) {
 #pragma unroll
-        for (int j = 0; j < 64; ++j) v[j] = 0u;
+        for (int q = 0; q < 128; ++q) v[q] = 0u;
       } else {
         tmem_ld32(ta, v);
         tmem_ld32(ta + 32u, v + 32);
+        if (G == 128) {
+          tmem_ld32(ta + 64u, v + 64);
+          tmem_ld32(ta + 96u, v + 96);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       }
-      if (d.counts) {
-        // counting semiring: every sum is an integer <= K <= 2^24, exact in
-        // FP32.  The warp's 32 rows x 64 counts go through shared memory (the
-        // operand ring is idle once every product is done; rows padded to 65
-        // words against bank conflicts) so that each store writes 32
-        // consecutive counts of one row.
-        if (ok && !*sfail) {
-          uint32_t* st = reinterpret_cast<uint32_t*>(smem) + ew * (32 * 65);
 #pragma unroll
-          for (int j = 0; j < 64; ++j) st[lane * 65 + j] = (uint32_t)__uint_as_float(v[j]);
-          __syncwarp();
-          const int64_t n0 = nt * BN + c * 64;
-          for (int rr = 0; rr < 32; ++rr) {
-            const int64_t mm = mt * kMmaBM + ew * 32 + rr;
-            if (mm >= d.M) break;
-            uint32_t* row = d.counts + (b * d.M + mm) * d.N;
-            if (n0 + lane < d.N) row[n0 + lane] = st[rr * 65 + lane];
-            if (n0 + 32 + lane < d.N) row[n0 + 32 + lane] = st[rr * 65 + 32 + lane];
+      for (int h = 0; h < 2; ++h) {
+        if (h * 64 >= G) break;
+        const uint32_t* vh = v + 64 * h;
+        const int c = (c0 >> 6) + h;  // 64-column chunk of the tile
+        if (d.counts) {
+          // counting semiring: every sum is an integer <= K <= 2^24, exact in
+          // FP32.  The warp's 32 rows x 64 counts go through shared memory (the
+          // operand ring is idle once every product is done; rows padded to 65
+          // words against bank conflicts) so that each store writes 32
+          // consecutive counts of one row.
+          if (store) {
+            uint32_t* st = reinterpret_cast<uint32_t*>(smem) + ew * (32 * 65);
+#pragma unroll
+            for (int q = 0; q < 64; ++q) st[lane * 65 + q] = (uint32_t)__uint_as_float(vh[q]);
+            __syncwarp();
+            const int64_t n0 = nt * BN + c * 64;
+            for (int rr = 0; rr < 32; ++rr) {
+              const int64_t mm = mt * kMmaBM + ew * 32 + rr;
+              if (mm >= d.M) break;
+              uint32_t* row = d.counts + (b * d.M + mm) * d.N;
+              if (n0 + lane < d.N) row[n0 + lane] = st[rr * 65 + lane];
+              if (n0 + 32 + lane < d.N) row[n0 + 32 + lane] = st[rr * 65 + 32 + lane];
+            }
+            __syncwarp();
           }
-          __syncwarp();
+          continue;
         }
-        continue;
-      }
-      uint64_t word = 0;
+        uint64_t word = 0;
 #pragma unroll
-      for (int j = 0; j < 64; ++j) word |= (uint64_t)(__uint_as_float(v[j]) > 0.0f) << j;
-      const int64_t w = nt * (BN / 64) + c;
-      if (ok && !*sfail && m < d.M && w < d.Nw) {
-        const int64_t rem = d.N - w * 64;
-        if (rem < 64) word &= (1ull << rem) - 1ull;
-        d.C[(b * d.M + m) * d.Nw + w] = word;
+        for (int q = 0; q < 64; ++q) word |= (uint64_t)(__uint_as_float(vh[q]) > 0.0f) << q;
+        const int64_t w = nt * (BN / 64) + c;
+        if (store && m < d.M && w < d.Nw) {
+          const int64_t rem = d.N - w * 64;
+          if (rem < 64) word &= (1ull << rem) - 1ull;
+          d.C[(b * d.M + m) * d.Nw + w] = word;
+        }
       }
     }
     if (!ok && lane == 0) atomicExch(d.err, 1);
@@ -555,6 +605,20 @@ int64_t unpack_blocks_b(const MmaDesc& d) {
 void launch_unpack(const MmaDesc* d_descs, int nprob, int64_t blocks_a, int64_t blocks_b,
                    cudaStream_t s) {
   if (nprob <= 0) return;
+  // the expansion kernels use no shared memory; asking for the largest
+  // shared-memory carveout anyway keeps the SMs in the configuration the
+  // contraction kernel that follows needs, so that no reconfiguration sits
+  // between the two launches
+  static bool carveout = [] {
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(unpack_rows_kernel),
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(unpack_transpose_kernel),
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    return true;
+  }();
+  (void)carveout;
   if (blocks_a > 0) unpack_rows_kernel<<<dim3((unsigned)blocks_a, (unsigned)nprob), 256, 0, s>>>(d_descs);
   if (blocks_b > 0)
     unpack_transpose_kernel<<<dim3((unsigned)blocks_b, (unsigned)nprob), 256, 0, s>>>(d_descs);
@@ -565,8 +629,18 @@ cudaError_t launch_mma(const MmaDesc* d_descs, const CUtensorMap* d_maps, const 
   if (nprob <= 0 || grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   smem_limit(reinterpret_cast<const void*>(mma_bool_kernel), kMmaSmem);
-  mma_bool_kernel<<<(unsigned)grid, kMmaThreads, kMmaSmem, s>>>(d_descs, d_maps, d_cta0, nprob);
-  return cudaGetLastError();
+  // programmatic dependent launch: the set-up overlaps the expansion kernel
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kMmaThreads);
+  cfg.dynamicSmemBytes = kMmaSmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mma_bool_kernel, d_descs, d_maps, d_cta0, nprob);
 }
 
 }  // namespace pa
