@@ -676,6 +676,10 @@ double rowor_cost_us(const pa_ctx* ctx, const JoinShape& js, double dens) {
   return dens * M * K * nb * ceil(N / 64) / rate_or + units / kRowOrUnitsPerUs;
 }
 
+// Bytes per microsecond the two expansion kernels write together (measured
+// on 2048 x 2048 operands of a GB300: 8.4 MB in 12 us).
+constexpr double kExpandBytesPerUs = 7.0e5;
+
 bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   // no context (pa_solve_network_static): the row-OR, which needs no byte copies
   if (!ctx || ctx->path == PA_PATH_ROWOR || tensor_map_encoder() == nullptr) return false;
@@ -688,7 +692,14 @@ bool use_mma(const pa_ctx* ctx, const JoinShape& js, double ra) {
   if (macs < 134217728.0) return false;  // small clusters: the row-OR's launch is cheaper
   const double dens = ra >= 0 ? ra : 0.05;
   const double t_or = rowor_cost_us(ctx, js, dens);
-  const double t_mma = macs / ctx->rate_mma;
+  // rate_mma is measured on a 2048^3 product, expansion of both operands
+  // included (2 x 2048^2 bytes for 2048^3 multiply-adds); a cluster whose
+  // operands are larger relative to its products (few rows and columns,
+  // many summed values) pays the bytes beyond that share at the expansion
+  // kernels' rate
+  const double bytes = nb * (M + N) * (ceil(K / 128) * 128);
+  const double extra = std::max(0.0, bytes - macs * (2.0 / 2048.0));
+  const double t_mma = macs / ctx->rate_mma + extra / kExpandBytesPerUs;
   return t_mma < t_or;
 }
 
@@ -788,6 +799,14 @@ BitArr join(Builder& bd, const BitArr& X, const BitArr& Y, const std::vector<int
     md.Ab = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.M * md.Kp)));
     md.Bb = static_cast<uint8_t*>(bd.alloc((size_t)(md.nbatch * md.N * md.Kp)));
     add_occupancy(bd, md);
+    if (md.ksplit > 1) {
+      // the CTAs of one tile OR their partial results into C
+      Op z;
+      z.kind = OP_MEMSET;
+      z.p = C.w;
+      z.count = C.words();
+      bd.emit(z);
+    }
     bd.pend_mma.push_back(md);
     bd.st.mma_macs += (double)js.nbatch * (double)js.M * js.nbits * (double)js.K;
     bd.st.n_mma++;

@@ -307,6 +307,8 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
   const int p = *sp;
   const MmaDesc& d = sd;
   int64_t t = (int64_t)blockIdx.x - cta0s[p];
+  const int kc = (int)(t % d.ksplit);
+  t /= d.ksplit;
   const int64_t nt = t % d.n_tiles;
   t /= d.n_tiles;
   const int64_t mt = t % d.m_tiles;
@@ -319,12 +321,17 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
   // issuer walk the same sequence, the j-th active block using ring slot j
   const uint32_t* occa = d.occ_a ? d.occ_a + (b * d.m_tiles + mt) * d.kb_words : nullptr;
   const uint32_t* occb = d.occ_b ? d.occ_b + (b * d.n_tiles + nt) * d.kb_words : nullptr;
-  const int kbw = (nk + 31) / 32;
+  // this CTA's K blocks [kb0, kb1) and the bitmap words that hold them
+  const int kb0 = kc * d.kchunk, kb1 = min(nk, kb0 + d.kchunk);
+  const int w0 = kb0 / 32, w1 = (kb1 + 31) / 32;
+  const bool split = d.ksplit > 1;
   auto active = [&](int w) -> uint32_t {
     uint32_t m = 0xffffffffu;
     if (occa) m &= __ldcg(occa + w);
     if (occb) m &= __ldcg(occb + w);
-    if (w == kbw - 1 && (nk & 31)) m &= (1u << (nk & 31)) - 1u;
+    const int lo = max(kb0 - 32 * w, 0), hi = min(kb1 - 32 * w, 32);
+    if (hi <= lo) return 0u;
+    m &= (hi == 32 ? 0xffffffffu : (1u << hi) - 1u) & ~((1u << lo) - 1u);
     return m;
   };
 
@@ -341,7 +348,7 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
       asm volatile("griddepcontrol.wait;" ::: "memory");
       int j = 0;
       bool failed = false;
-      for (int w = 0; w < kbw && !failed; ++w) {
+      for (int w = w0; w < w1 && !failed; ++w) {
         for (uint32_t m = active(w); m; m &= m - 1) {
           const int k = w * 32 + __ffs(m) - 1;
           const int s = j % kMmaStages;
@@ -385,7 +392,7 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
       const uint32_t idesc = f8_idesc(kMmaBM, BN);
       int j = 0;
       bool failed = false;
-      for (int w = 0; w < kbw && !failed; ++w) {
+      for (int w = w0; w < w1 && !failed; ++w) {
         for (uint32_t m = active(w); m; m &= m - 1) {
           const int s = j % kMmaStages;
           const uint32_t ph = (uint32_t)(j / kMmaStages) & 1u;
@@ -426,10 +433,12 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
     // no K block in common: nothing was accumulated, every sum is zero
     // (decided while the products run)
     bool none = true;
-    for (int w = 0; w < kbw && none; ++w) none = (active(w) == 0);
+    for (int w = w0; w < w1 && none; ++w) none = (active(w) == 0);
     const bool ok = bar_wait(accum, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool store = ok && !*sfail;
+    // with K split, a CTA that summed nothing leaves C as it is (other CTAs
+    // OR their bits into the same words)
+    const bool store = ok && !*sfail && !(split && none);
     const int64_t m = mt * kMmaBM + ew * 32 + lane;
     // up to 128 columns per round: every TMEM load of the round is in flight
     // before the one wait
@@ -484,7 +493,9 @@ mma_bool_kernel(const MmaDesc* __restrict__ descs, const CUtensorMap* __restrict
         if (store && m < d.M && w < d.Nw) {
           const int64_t rem = d.N - w * 64;
           if (rem < 64) word &= (1ull << rem) - 1ull;
-          d.C[(b * d.M + m) * d.Nw + w] = word;
+          uint64_t* dst = d.C + (b * d.M + m) * d.Nw + w;
+          if (!split) *dst = word;
+          else if (word) atomicOr(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)word);
         }
       }
     }
@@ -563,14 +574,30 @@ void mma_plan(MmaDesc& d) {
   d.Kp = (d.K + kMmaBK - 1) / kMmaBK * kMmaBK;
   d.m_tiles = (d.M + kMmaBM - 1) / kMmaBM;
   d.n_tiles = (d.N + d.BN - 1) / d.BN;
-  d.kb_words = (d.Kp / kMmaBK + 31) / 32;
+  const int64_t nk = d.Kp / kMmaBK;
+  d.kb_words = (nk + 31) / 32;
+  // Few output tiles and a long K (a cluster that sums many variables into a
+  // small result) would leave most SMs idle: split K over up to one CTA per
+  // SM, each with at least 8 K blocks.  Only for the Boolean product, whose
+  // partial results combine by OR.
+  d.ksplit = 1;
+  d.kchunk = (int32_t)nk;
+  const int64_t tiles = d.nbatch * d.m_tiles * d.n_tiles;
+  if (!d.counts && tiles < 152) {
+    const int64_t want = std::min<int64_t>(152 / tiles, nk / 8);
+    if (want > 1) {
+      const int64_t chunk = (nk + want - 1) / want;
+      d.kchunk = (int32_t)chunk;
+      d.ksplit = (int32_t)((nk + chunk - 1) / chunk);
+    }
+  }
 }
 
 int64_t mma_occ_words(const MmaDesc& d) {
   return d.nbatch * (d.m_tiles + d.n_tiles) * d.kb_words;
 }
 
-int64_t mma_ctas(const MmaDesc& d) { return d.nbatch * d.m_tiles * d.n_tiles; }
+int64_t mma_ctas(const MmaDesc& d) { return d.nbatch * d.m_tiles * d.n_tiles * d.ksplit; }
 
 size_t mma_smem_bytes() { return kMmaSmem; }
 

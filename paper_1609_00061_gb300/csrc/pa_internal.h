@@ -271,6 +271,10 @@ struct MmaDesc {
   uint32_t* occ_a;
   uint32_t* occ_b;
   int64_t kb_words;
+  // K split: ksplit CTAs per output tile, each summing kchunk consecutive
+  // 128-value K blocks and OR-ing its bits into C, which starts at zero
+  // (Boolean products only; 1 when every tile is summed by one CTA)
+  int32_t ksplit, kchunk;
 };
 // 32-bit words of the two occupancy bitmaps of a planned problem
 int64_t mma_occ_words(const MmaDesc& d);

@@ -36,6 +36,12 @@ MMA_CASES = [
     ((0, 1), (1, 2), (0, 2), {0: 70, 1: 70, 2: 100}),       # 128-column tiles
     ((0, 1, 2), (0, 2, 3), (0, 1, 3), {0: 3, 1: 200, 2: 150, 3: 300}),  # batch axis
     ((0, 1), (1, 2), (0, 2), {0: 1024, 1: 1024, 2: 1024}),  # several tiles each way
+    # few output tiles and a long K: K split over several CTAs per tile, their
+    # partial results OR-ed into C (a ragged last K block, a batch axis, and
+    # two summed variables of 256 x 64)
+    ((0, 1), (1, 2), (0, 2), {0: 200, 1: 5000, 2: 300}),
+    ((0, 1, 2), (0, 2, 3), (0, 1, 3), {0: 3, 1: 100, 2: 3000, 3: 64}),
+    ((0, 1, 2), (1, 2, 3), (0, 3), {0: 64, 1: 256, 2: 64, 3: 100}),
 ]
 
 
