@@ -64,6 +64,13 @@ class Clocks:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes the host (and a driver query) while it starts:
+        # wait for its first sample, so that the timed steps run with the
+        # sampler already in its loop
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -580,6 +587,10 @@ def run_ours(args, rank, world, local_rank):
     step_ms = []
     clocks = Clocks(dev)
     clocks.start()
+    for _ in range(3):  # untimed, with the sampler running and the flush loaded
+        flush.fill_(0)
+        step()
+    torch.cuda.synchronize()
     ms, st, _ = timed_steps(False)
     ms_prof, _, kernels = timed_steps(True)
     if dist:

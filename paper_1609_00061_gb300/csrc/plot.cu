@@ -172,6 +172,7 @@ __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i)
 // exact FP64 evaluation.  Bits are set directly in the thread's word, so no
 // warp vote is needed and a row's words are stored coalesced.
 constexpr int kPlotThreads = 256;
+static_assert(sizeof(PlotJob) % 4 == 0, "plot descriptors are copied as 32-bit words");
 constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
 
 __device__ __forceinline__ int ypad(int i) { return i + (i >> 6); }
@@ -293,8 +294,18 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   float* g32s = reinterpret_cast<float*>(g64s + (size_t)rmax * gstride);
   float4* thrs = reinterpret_cast<float4*>(plot_smem + plot_thr_offset(rmax, gstride));
   float* ytab = reinterpret_cast<float*>(thrs + rmax);
+  // The block's job and a copy of its descriptor in shared memory: every
+  // global read of the set-up is one round trip on the block's critical path
+  // (the descriptors were just uploaded), so the jobs' first tiles are
+  // compared by one thread each instead of a binary search, and the
+  // descriptor's fields are read from shared memory afterwards.
+  __shared__ PlotJob sJ;
   __shared__ int s_job;
-  if (threadIdx.x == 0) {
+  if (njobs <= (int)blockDim.x) {
+    const int below = (threadIdx.x < njobs && jobs[threadIdx.x].tile0 <= (int64_t)blockIdx.x);
+    const int n = __syncthreads_count(below);  // tile0 ascends from 0
+    if (threadIdx.x == 0) s_job = n - 1;
+  } else if (threadIdx.x == 0) {
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
@@ -303,7 +314,13 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
     s_job = lo;
   }
   __syncthreads();
-  const PlotJob* J = jobs + s_job;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs + s_job);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sJ);
+    for (int i = threadIdx.x; i < (int)(sizeof(PlotJob) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const PlotJob* J = &sJ;
   const int D = DS >= 0 ? DS : J->degree;
   const int row_words = (int)J->row_words;
   const int res_last = J->res[J->ndim - 1];
@@ -315,9 +332,11 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   const int arity = J->arity;
   const double ylo = J->lo[arity - 1], ydelta = J->delta[arity - 1];
   if (hoisted) {
-    // set-up: the centre table, and per row (one thread each) the row
-    // polynomial g_0..g_D in FP64 (the inner nested sums of the pa.h order),
-    // its FP32 copy and the row's thresholds eps -+ B_row
+    // set-up: per row (one thread each) the row polynomial g_0..g_D in FP64
+    // (the inner nested sums of the pa.h order), its FP32 copy and the row's
+    // thresholds eps -+ B_row.  (One thread per (row, j) evaluates every
+    // port's centre D + 1 times: slower where the FP64 pipe is the limit, as
+    // in the set-up of large 3-D plots.)
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
       int64_t rest = row0 + r;
       int64_t idx[kMaxDim];
@@ -357,8 +376,21 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
   // share; a block's share is small next to its plot tile)
   if (zero_words > 0) clear_ranges(zr, nzero, zero_words);
   if (hoisted) {
-    if (ysmem)
-      for (int i = threadIdx.x; i < res_last; i += blockDim.x) ytab[ypad(i)] = J->y32[i];
+    if (ysmem) {
+      // eight loads in flight per thread before the stores (a load-store
+      // loop waits out the L2 latency once per element)
+      const float* __restrict__ yg = J->y32;
+      const int bs = blockDim.x;
+      int i = threadIdx.x;
+      for (; i + 7 * bs < res_last; i += 8 * bs) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = yg[i + k * bs];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ytab[ypad(i + k * bs)] = v[k];
+      }
+      for (; i < res_last; i += bs) ytab[ypad(i)] = yg[i];
+    }
     __syncthreads();
   }
   const int kind = J->kind, strict = J->strict;
