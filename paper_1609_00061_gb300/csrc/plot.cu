@@ -121,6 +121,55 @@ __device__ __forceinline__ double nest_rows(int k, int rem, const double*& cp, c
   }
 }
 
+// The row polynomial g_0..g_DS of a 2- or 3-port relation at one row, for a
+// degree fixed at compile time: the very products and sums of nest_t, in the
+// same order, with the powers of the row ports (1, x, x*x, ... by repeated
+// multiplication, the same sequence nest_t forms for every sum) computed once
+// instead of once per sum, and every sum unrolled, so that the sums of the
+// D + 1 blocks proceed side by side rather than one FP64 chain after another.
+template <int DS>
+__device__ __forceinline__ void row_poly2(const double* __restrict__ cp, double x0, double* g) {
+  double p0[DS + 1];
+  p0[0] = 1.0;
+#pragma unroll
+  for (int e = 1; e <= DS; ++e) p0[e] = __dmul_rn(p0[e - 1], x0);
+#pragma unroll
+  for (int j = 0; j <= DS; ++j) {
+    double s0 = __dmul_rn(cp[0], p0[0]);
+#pragma unroll
+    for (int e = 1; e <= DS - j; ++e) s0 = __dadd_rn(s0, __dmul_rn(cp[e], p0[e]));
+    cp += DS - j + 1;
+    g[j] = s0;
+  }
+}
+
+template <int DS>
+__device__ __forceinline__ void row_poly3(const double* __restrict__ cp, double x0, double x1,
+                                          double* g) {
+  double p0[DS + 1], p1[DS + 1];
+  p0[0] = 1.0;
+  p1[0] = 1.0;
+#pragma unroll
+  for (int e = 1; e <= DS; ++e) {
+    p0[e] = __dmul_rn(p0[e - 1], x0);
+    p1[e] = __dmul_rn(p1[e - 1], x1);
+  }
+#pragma unroll
+  for (int j = 0; j <= DS; ++j) {
+    double s1 = 0.0;
+#pragma unroll
+    for (int e1 = 0; e1 <= DS - j; ++e1) {
+      double s0 = __dmul_rn(cp[0], p0[0]);
+#pragma unroll
+      for (int e = 1; e <= DS - j - e1; ++e) s0 = __dadd_rn(s0, __dmul_rn(cp[e], p0[e]));
+      cp += DS - j - e1 + 1;
+      const double term = __dmul_rn(s0, p1[e1]);
+      s1 = (e1 == 0) ? term : __dadd_rn(s1, term);
+    }
+    g[j] = s1;
+  }
+}
+
 __device__ __forceinline__ double centre(double lo, double delta, int64_t i) {
   return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), delta));
 }
@@ -283,7 +332,7 @@ __device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, f
 }
 
 template <int DS>
-__global__ void __launch_bounds__(kPlotThreads)
+__global__ void __launch_bounds__(kPlotThreads, 3)
 plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstride, int rmax,
             const ZeroRange* __restrict__ zr, int nzero, int64_t zero_words) {
   extern __shared__ __align__(16) unsigned char plot_smem[];
@@ -350,7 +399,24 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
       const double* cp = J->coeffs;
       const float Y = J->ymax;
       float a = 0.0f, pw = 1.0f;
-      for (int j = 0; j <= D; ++j) {
+      bool done = false;
+      if constexpr (DS >= 0) {
+        if (arity == 2 || arity == 3) {
+          double gv[DS + 1];
+          if (arity == 2) row_poly2<DS>(cp, x[0], gv);
+          else row_poly3<DS>(cp, x[0], x[1], gv);
+#pragma unroll
+          for (int j = 0; j <= DS; ++j) {
+            const float g1 = __double2float_rn(gv[j]);
+            g64s[r * gstride + j] = gv[j];
+            g32s[r * gstride + j] = g1;
+            a = __fmaf_rn(fabsf(g1), pw, a);
+            pw = __fmul_rn(pw, Y);
+          }
+          done = true;
+        }
+      }
+      for (int j = 0; !done && j <= D; ++j) {
         const double g = nest_rows(arity - 2, D - j, cp, x);  // cp walks block j
         const float g1 = __double2float_rn(g);
         g64s[r * gstride + j] = g;
