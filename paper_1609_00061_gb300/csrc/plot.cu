@@ -215,11 +215,12 @@ __device__ __noinline__ bool general64(const PlotJob* J, int64_t row, int64_t i)
 // One block plots a tile of rows.  Set-up: the FP32 centres of the last axis
 // are staged in shared memory (padded so that consecutive words hit distinct
 // banks) and each row's polynomial and thresholds are computed there.  Then
-// each thread takes whole output words: the whole-word test first, else the
-// 64 pixels in FP32 (f = g_0 + g_1 y + ... by fused multiply-adds); |f| below
-// eps - B_row is on, above eps + B_row is off, anything else is decided by the
-// exact FP64 evaluation.  Bits are set directly in the thread's word, so no
-// warp vote is needed and a row's words are stored coalesced.
+// Taylor tests decide whole spans and words first (each thread a span of
+// four words, then its words); the words no test decides are listed, and the
+// block evaluates them, a piece of each word per thread, in FP32
+// (f = g_0 + g_1 y + ... by fused multiply-adds): |f| below eps - B_row is on,
+// above eps + B_row is off, anything else is decided by the exact FP64
+// evaluation.
 constexpr int kPlotThreads = 256;
 static_assert(sizeof(PlotJob) % 4 == 0, "plot descriptors are copied as 32-bit words");
 constexpr int kYTabCap = 12288;  // largest last axis whose centres are staged in shared memory
@@ -231,8 +232,6 @@ __host__ __device__ __forceinline__ size_t plot_thr_offset(int rmax, int gstride
   return ((size_t)rmax * gstride * 12 + 15) / 16 * 16;
 }
 
-// The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
-// certainly on, bit b of *pending when only the FP64 evaluation can decide.
 // The FP32 centre of last-axis pixel i.
 __device__ __forceinline__ float ycentre32(double ylo, double ydelta, int i) {
   return __double2float_rn(centre(ylo, ydelta, i));
@@ -285,6 +284,8 @@ __device__ __forceinline__ void clear_ranges(const ZeroRange* __restrict__ zr, i
   }
 }
 
+// The 64 pixels of one word in FP32: bit b of *on is set when the pixel is
+// certainly on, bit b of *pending when only the FP64 evaluation can decide.
 template <int DS, bool EQ, bool YS, bool FULL>
 __device__ __forceinline__ void eval_word(const float* g, int D, float lo, float hi,
                                           const float* ytab_w, const float* __restrict__ y32g,
@@ -329,6 +330,43 @@ __device__ __forceinline__ void eval_word_any(const float* g, int D, float lo, f
                                               int nb, uint64_t* on, uint64_t* pending) {
   if (nb == 64) eval_word<DS, EQ, YS, true>(g, D, lo, hi, ytab_w, y32g, i0, nb, on, pending);
   else eval_word<DS, EQ, YS, false>(g, D, lo, hi, ytab_w, y32g, i0, nb, on, pending);
+}
+
+// Eight pixels of a row in FP32 (f = g_0 + g_1 y + ... by fused
+// multiply-adds): bit b of the result is set when pixel b is certainly on,
+// bit b of *pending when only the FP64 evaluation can decide.  nb8 pixels
+// (1..8) exist; y comes from the padded shared table (YS) or global memory.
+template <int DS, bool EQ, bool YS>
+__device__ __forceinline__ uint32_t eval8(const float* g, int D, float lo, float hi,
+                                          const float* yt, const float* __restrict__ yg, int ic,
+                                          int nb8, uint32_t* pending) {
+  uint32_t on = 0, pe = 0;
+#pragma unroll
+  for (int bb = 0; bb < 8; ++bb) {
+    if (bb < nb8) {
+      const float y = YS ? yt[bb] : __ldg(yg + ic + bb);
+      float s = g[0], pw = y;
+      if (DS >= 0) {
+#pragma unroll
+        for (int j = 1; j <= (DS >= 0 ? DS : 1); ++j) {
+          if (j > 1) pw = __fmul_rn(pw, y);
+          s = __fmaf_rn(g[j], pw, s);
+        }
+      } else {
+        for (int j = 1; j <= D; ++j) {
+          if (j > 1) pw = __fmul_rn(pw, y);
+          s = __fmaf_rn(g[j], pw, s);
+        }
+      }
+      const float dd = EQ ? fabsf(s) : s;
+      const bool c_on = dd < lo;
+      const bool c_pe = !c_on && !(dd > hi);
+      on |= (uint32_t)c_on << bb;
+      pe |= (uint32_t)c_pe << bb;
+    }
+  }
+  *pending = pe;
+  return on;
 }
 
 template <int DS>
@@ -556,40 +594,98 @@ plot_kernel(const PlotJob* __restrict__ jobs, int njobs, int ytab_cap, int gstri
     }
   }
   __syncthreads();
-  // Phase 2: pixel by pixel
+  // Phase 2: pixel by pixel.  A block with few undecided words (a curve
+  // crossing some of its rows) cuts each into C = 8 pieces of 8 pixels, one
+  // per thread, so that they spread over its threads; otherwise each thread
+  // takes whole words (C = 1), whose 64 pixels it evaluates with more
+  // independent work in flight and one set-up per word.
   const int nlist = s_n;
-  for (int e = threadIdx.x; e < nlist; e += blockDim.x) {
-    const int f = list[e];
+  const int nthr = (int)blockDim.x;
+  const int C = 4 * nlist <= nthr ? 8 : 1;
+  const int PC = 64 / C;
+  if (C == 1) {
+    for (int e = threadIdx.x; e < nlist; e += nthr) {
+      const int f = list[e];
+      const int r = f / row_words, w = f - r * row_words;
+      const int64_t row = row0 + r;
+      const int i0 = w * 64;
+      const int nb = min(64, res_last - i0);
+      uint64_t word = 0;
+      if (hoisted) {
+        float g[kG];
+        load_g(r, g);
+        const float4 th = thrs[r];
+        const float lo = th.x, hi = th.y;
+        uint64_t pending = 0;
+        const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
+        if (kind == PA_EQ) {
+          if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+          else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+        } else {
+          if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+          else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
+        }
+        while (pending) {
+          const int bb = __ffsll((long long)pending) - 1;
+          pending &= pending - 1;
+          if (exact64(centre(ylo, ydelta, i0 + bb), g64s + r * gstride, D, kind, eps, strict))
+            word |= (1ull << bb);
+        }
+      } else {
+        for (int bb = 0; bb < nb; ++bb)
+          if (general64(J, row, i0 + bb)) word |= (1ull << bb);
+      }
+      out[row * row_words + w] = word;
+    }
+  }
+  for (int e = threadIdx.x; C > 1 && e < nlist * C; e += nthr) {
+    const int f = list[e / C], c = e % C;
     const int r = f / row_words, w = f - r * row_words;
     const int64_t row = row0 + r;
-    const int i0 = w * 64;
-    const int nb = min(64, res_last - i0);
-    uint64_t word = 0;
+    const int ic0 = w * 64 + PC * c;  // first pixel of the piece
+    uint64_t bits = 0;
+    float g[kG];
+    float lo = 0.0f, hi = 0.0f;
     if (hoisted) {
-      float g[kG];
       load_g(r, g);
       const float4 th = thrs[r];
-      const float lo = th.x, hi = th.y;
-      uint64_t pending = 0;
-      const float* ytab_w = ytab + i0 + w;  // ypad(i0 + b) = i0 + w + b
-      if (kind == PA_EQ) {
-        if (ysmem) eval_word_any<DS, true, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
-        else eval_word_any<DS, true, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
-      } else {
-        if (ysmem) eval_word_any<DS, false, true>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
-        else eval_word_any<DS, false, false>(g, D, lo, hi, ytab_w, y32, i0, nb, &word, &pending);
-      }
-      while (pending) {
-        const int bb = __ffsll((long long)pending) - 1;
-        pending &= pending - 1;
-        if (exact64(centre(ylo, ydelta, i0 + bb), g64s + r * gstride, D, kind, eps, strict))
-          word |= (1ull << bb);
-      }
-    } else {
-      for (int bb = 0; bb < nb; ++bb)
-        if (general64(J, row, i0 + bb)) word |= (1ull << bb);
+      lo = th.x;
+      hi = th.y;
     }
-    out[row * row_words + w] = word;
+    for (int g8 = 0; g8 < PC / 8; ++g8) {
+      const int ic = ic0 + 8 * g8;
+      const int nb8 = min(8, res_last - ic);  // <= 0: padding past the row
+      if (nb8 <= 0) break;
+      uint32_t b8 = 0;
+      if (hoisted) {
+        uint32_t pending = 0;
+        const float* yt = ytab + ic + w;  // ypad(ic + b) = ic + w + b
+        if (kind == PA_EQ) {
+          if (ysmem) b8 = eval8<DS, true, true>(g, D, lo, hi, yt, y32, ic, nb8, &pending);
+          else b8 = eval8<DS, true, false>(g, D, lo, hi, yt, y32, ic, nb8, &pending);
+        } else {
+          if (ysmem) b8 = eval8<DS, false, true>(g, D, lo, hi, yt, y32, ic, nb8, &pending);
+          else b8 = eval8<DS, false, false>(g, D, lo, hi, yt, y32, ic, nb8, &pending);
+        }
+        while (pending) {
+          const int bb = __ffs(pending) - 1;
+          pending &= pending - 1;
+          if (exact64(centre(ylo, ydelta, ic + bb), g64s + r * gstride, D, kind, eps, strict))
+            b8 |= 1u << bb;
+        }
+      } else {
+        for (int bb = 0; bb < nb8; ++bb)
+          if (general64(J, row, ic + bb)) b8 |= 1u << bb;
+      }
+      bits |= (uint64_t)b8 << (8 * g8);
+    }
+    uint64_t* ow = out + row * row_words + w;
+    switch (C) {
+      case 1: *ow = bits; break;
+      case 2: reinterpret_cast<uint32_t*>(ow)[c] = (uint32_t)bits; break;
+      case 4: reinterpret_cast<uint16_t*>(ow)[c] = (uint16_t)bits; break;
+      default: reinterpret_cast<uint8_t*>(ow)[c] = (uint8_t)bits; break;
+    }
   }
 }
 
