@@ -1174,22 +1174,23 @@ std::vector<BitArr> plot_poly(Builder& bd, const std::vector<PlotReq>& reqs) {
   std::vector<BitArr> plots;
   std::vector<PlotJob> jobs(nrel);
   std::vector<size_t> coeff_off(nrel);
-  // Words per block: about 2048, so that a block's set-up (row polynomials,
-  // centre table copy) is spread over many words; 1024 when that would leave
-  // fewer than three blocks per SM (a call with a few large plots), so that
-  // every SM holds several blocks.
+  // Words per block: the plots' words spread over the blocks the GPU holds
+  // at once (so that no second wave of blocks waits for the first), between
+  // 256 (enough words to carry a block's set-up: row polynomials, centre
+  // table copy) and 2048.
   int64_t tile_words = 2048;
   {
-    int64_t blocks = 0;
+    int64_t words = 0;
+    int common = reqs[0].rel->degree;
     for (const PlotReq& q : reqs) {
       const std::vector<int> dv = distinct_vars(*q.rel);
       int64_t nrows = 1;
       for (size_t k = 0; k + 1 < dv.size(); ++k) nrows *= q.axes[dv[k]].res;
-      const int64_t rw = (q.axes[dv.back()].res + 63) / 64;
-      const int64_t rpt = std::max<int64_t>(1, std::min<int64_t>(256, 2048 / rw));
-      blocks += (nrows + rpt - 1) / rpt;
+      words += nrows * ((q.axes[dv.back()].res + 63) / 64);
+      if (q.rel->degree != common) common = -1;
     }
-    if (blocks < 3 * 152) tile_words = 1024;
+    const int64_t slots = plot_resident_blocks(common >= 1 && common <= 4 ? common : -1);
+    tile_words = std::min<int64_t>(2048, std::max<int64_t>(256, (words + slots - 1) / slots));
   }
   int64_t tiles = 0, max_tile_words = 1, ycen = 0;
   std::vector<CentreTab> tabs;  // one per distinct last-port axis of the hoisted jobs
@@ -1262,7 +1263,8 @@ std::vector<BitArr> plot_poly(Builder& bd, const std::vector<PlotReq>& reqs) {
         off += (int32_t)coeff_count(r.arity - 1, r.degree - j);
       }
     }
-    J.rows_per_tile = (int32_t)std::max<int64_t>(1, std::min<int64_t>(256, tile_words / J.row_words));
+    J.rows_per_tile = (int32_t)std::max<int64_t>(
+        1, std::min<int64_t>(256, (tile_words + J.row_words - 1) / J.row_words));
     J.tile0 = tiles;
     tiles += (J.nrows + J.rows_per_tile - 1) / J.rows_per_tile;
     max_rows = std::max(max_rows, J.rows_per_tile);

@@ -117,6 +117,8 @@ void launch_plot_centres(const CentreTab* d_tabs, int ntabs, int64_t total_items
 // The same launch also clears the `nzero` ranges (zero_words words in all)
 // that later contractions OR their results into, so that no separate memset
 // sits between the launches.
+// Plot blocks the GPU holds at once (all SMs), for the kernel of this degree.
+int plot_resident_blocks(int common_degree);
 void launch_plot(const PlotJob* d_jobs, int njobs, int64_t total_tiles, int max_rows_per_tile,
                  int max_degree, int common_degree, int max_res_last, int64_t max_tile_words,
                  const ZeroRange* d_zero, int nzero, int64_t zero_words, cudaStream_t s);

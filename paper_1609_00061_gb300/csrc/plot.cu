@@ -41,6 +41,8 @@
 #include <float.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "expr_eval.cuh"
 #include "pa_internal.h"
@@ -765,6 +767,46 @@ void launch_plot_corner(const CornerJob* d_jobs, int njobs, int64_t total_words,
   int64_t blocks = (bytes + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   plot_corner_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, bytes);
+}
+
+// Blocks of the plot kernel (of this degree) that the GPU holds at once:
+// per SM as the occupancy calculator gives it for 256 threads and a typical
+// 16 KB of shared memory (registers are the limit), times the SMs.  Cached;
+// 3 x 152 when the device cannot be asked.
+int plot_resident_blocks(int common_degree) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 3 * 152;
+  }
+  const std::pair<int, int> key(dev, common_degree);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const void* fn;
+  switch (common_degree) {
+    case 1: fn = reinterpret_cast<const void*>(plot_kernel<1>); break;
+    case 2: fn = reinterpret_cast<const void*>(plot_kernel<2>); break;
+    case 3: fn = reinterpret_cast<const void*>(plot_kernel<3>); break;
+    case 4: fn = reinterpret_cast<const void*>(plot_kernel<4>); break;
+    default: fn = reinterpret_cast<const void*>(plot_kernel<-1>); break;
+  }
+  int sms = 0, per = 0;
+  int v = 3 * 152;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kPlotThreads, 16 * 1024) ==
+          cudaSuccess &&
+      sms > 0 && per > 0)
+    v = sms * per;
+  else
+    cudaGetLastError();
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = v;
+  return v;
 }
 
 cudaError_t probe_kernel_image() {
