@@ -35,10 +35,15 @@ struct pa_ctx {
   size_t cap = 0;
   char* arena = nullptr;
   size_t arena_size = 0;
-  char* h_stage = nullptr;  // pinned staging for descriptor uploads
-  size_t h_stage_size = 0;
-  cudaEvent_t stage_done = nullptr;
-  bool stage_pending = false;
+  // pinned staging for descriptor uploads: a ring of slots, so that a call
+  // waits only for the upload kNStage calls back (the host may run that many
+  // calls ahead of the device)
+  static constexpr int kNStage = 4;
+  char* h_stage[kNStage] = {};
+  size_t h_stage_size[kNStage] = {};
+  cudaEvent_t stage_done[kNStage] = {};
+  bool stage_pending[kNStage] = {};
+  int stage_next = 0;
   std::string err;
   int* d_err = nullptr;                  // device error word written by bounded waits
   unsigned long long* d_stat = nullptr;  // words OR-ed by contractions (timing mode)
@@ -132,6 +137,15 @@ struct Memo {
   std::vector<Op> ops;
   std::vector<char> blob;
   pa_stats st{};
+  // the launches captured as one CUDA graph on the second call with the key
+  // (the descriptor upload stays a copy of its own before each launch)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool capture_failed = false;
+  ~Memo() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
 };
 
 // Builds the workspace layout, the descriptor blob and the launch list of a call.
@@ -1643,10 +1657,11 @@ pa_status ensure_arena(pa_ctx* ctx, size_t need) {
     return set_err(ctx, PA_ERR_OOM, "workspace of " + std::to_string(need) +
                                         " bytes exceeds the context's cap");
   }
-  if (ctx->stage_pending) {
-    cudaEventSynchronize(ctx->stage_done);
-    ctx->stage_pending = false;
-  }
+  for (int i = 0; i < pa_ctx::kNStage; ++i)
+    if (ctx->stage_pending[i]) {
+      cudaEventSynchronize(ctx->stage_done[i]);
+      ctx->stage_pending[i] = false;
+    }
   if (ctx->arena) {
     cudaDeviceSynchronize();  // the old arena may still be in use by queued work
     cudaFree(ctx->arena);
@@ -1667,23 +1682,27 @@ pa_status ensure_arena(pa_ctx* ctx, size_t need) {
 // Copy the blob into the arena through the pinned stage, on the stream.
 void upload_blob(pa_ctx* ctx, const std::vector<char>& blob, cudaStream_t s) {
   if (blob.empty()) return;
-  if (ctx->stage_pending) {
-    check_cuda(ctx, cudaEventSynchronize(ctx->stage_done), "cudaEventSynchronize");
-    ctx->stage_pending = false;
+  const int i = ctx->stage_next;
+  ctx->stage_next = (i + 1) % pa_ctx::kNStage;
+  if (ctx->stage_pending[i]) {
+    check_cuda(ctx, cudaEventSynchronize(ctx->stage_done[i]), "cudaEventSynchronize");
+    ctx->stage_pending[i] = false;
   }
-  if (ctx->h_stage_size < blob.size()) {
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    ctx->h_stage = nullptr;
-    ctx->h_stage_size = 0;
+  if (ctx->h_stage_size[i] < blob.size()) {
+    if (ctx->h_stage[i]) cudaFreeHost(ctx->h_stage[i]);
+    ctx->h_stage[i] = nullptr;
+    ctx->h_stage_size[i] = 0;
     const size_t sz = std::max<size_t>(blob.size() * 2, 1 << 16);
-    check_cuda(ctx, cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage), sz), "cudaMallocHost");
-    ctx->h_stage_size = sz;
+    check_cuda(ctx, cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage[i]), sz),
+               "cudaMallocHost");
+    ctx->h_stage_size[i] = sz;
   }
-  memcpy(ctx->h_stage, blob.data(), blob.size());
-  check_cuda(ctx, cudaMemcpyAsync(ctx->arena, ctx->h_stage, blob.size(), cudaMemcpyHostToDevice, s),
+  memcpy(ctx->h_stage[i], blob.data(), blob.size());
+  check_cuda(ctx,
+             cudaMemcpyAsync(ctx->arena, ctx->h_stage[i], blob.size(), cudaMemcpyHostToDevice, s),
              "cudaMemcpyAsync");
-  check_cuda(ctx, cudaEventRecord(ctx->stage_done, s), "cudaEventRecord");
-  ctx->stage_pending = true;
+  check_cuda(ctx, cudaEventRecord(ctx->stage_done[i], s), "cudaEventRecord");
+  ctx->stage_pending[i] = true;
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -1714,7 +1733,10 @@ pa_status run_call(pa_ctx* ctx, cudaStream_t s, pa_stats* stats, F&& body,
     bd.st.n_launches = (int32_t)bd.ops.size();
     if (stats) *stats = bd.st;
     if (memo_key) {
-      if (!ctx->memo) ctx->memo = new Memo();
+      // a new program: the old one's graph goes with it (an executable graph
+      // still running is freed when it completes)
+      delete ctx->memo;
+      ctx->memo = new Memo();
       Memo& m = *ctx->memo;
       m.key.swap(*memo_key);
       m.ops = std::move(bd.ops);
@@ -1797,7 +1819,39 @@ pa_status run_memo(pa_ctx* ctx, cudaStream_t s, pa_stats* stats) {
     }
     Memo& m = *ctx->memo;
     upload_blob(ctx, m.blob, s);
-    run_ops(ctx, m.ops, ctx->arena, s, ctx->prof);
+    if (ctx->prof || m.capture_failed) {
+      // per-launch timing needs the launches one by one
+      run_ops(ctx, m.ops, ctx->arena, s, ctx->prof);
+    } else {
+      if (!m.exec) {
+        // capture the launches once, on a stream of their own
+        cudaStream_t cs = nullptr;
+        bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          try {
+            run_ops(ctx, m.ops, ctx->arena, cs, false);
+          } catch (const Fail&) {
+            ok = false;
+          }
+          cudaGraph_t g = nullptr;
+          ok = (cudaStreamEndCapture(cs, &g) == cudaSuccess) && ok;
+          m.graph = g;
+          ok = ok && g && cudaGraphInstantiate(&m.exec, g, 0) == cudaSuccess;
+        }
+        if (cs) cudaStreamDestroy(cs);
+        if (!ok) {
+          cudaGetLastError();
+          if (m.exec) cudaGraphExecDestroy(m.exec);
+          m.exec = nullptr;
+          m.capture_failed = true;
+          run_ops(ctx, m.ops, ctx->arena, s, false);
+          if (stats) *stats = m.st;
+          return PA_OK;
+        }
+      }
+      check_cuda(ctx, cudaGraphLaunch(m.exec, s), "cudaGraphLaunch");
+    }
     if (stats) *stats = m.st;
     return PA_OK;
   } catch (const Fail& f) {
@@ -2263,13 +2317,17 @@ pa_status pa_create(pa_ctx** out, int device, size_t workspace_cap) {
   pa_ctx* ctx = new pa_ctx();
   ctx->device = device;
   ctx->cap = workspace_cap;
-  if (cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming) != cudaSuccess ||
+  bool ev_ok = true;
+  for (int i = 0; i < pa_ctx::kNStage; ++i)
+    ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->stage_done[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ev_ok ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_err), sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_stat), sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(ctx->d_stat, 0, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
-    if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
+    for (int i = 0; i < pa_ctx::kNStage; ++i)
+      if (ctx->stage_done[i]) cudaEventDestroy(ctx->stage_done[i]);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_stat) cudaFree(ctx->d_stat);
     delete ctx;
@@ -2282,13 +2340,17 @@ pa_status pa_create(pa_ctx** out, int device, size_t workspace_cap) {
 void pa_destroy(pa_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_done);
+  for (int i = 0; i < pa_ctx::kNStage; ++i)
+    if (ctx->stage_pending[i]) cudaEventSynchronize(ctx->stage_done[i]);
+  delete ctx->memo;  // its graph before the arena it points into
+  ctx->memo = nullptr;
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_stat) cudaFree(ctx->d_stat);
-  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-  if (ctx->stage_done) cudaEventDestroy(ctx->stage_done);
-  delete ctx->memo;
+  for (int i = 0; i < pa_ctx::kNStage; ++i) {
+    if (ctx->h_stage[i]) cudaFreeHost(ctx->h_stage[i]);
+    if (ctx->stage_done[i]) cudaEventDestroy(ctx->stage_done[i]);
+  }
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
 }
