@@ -118,6 +118,30 @@ __global__ void reshape_words_kernel(const ReshapeDesc* __restrict__ descs,
   const I total = (I)(d.out_nrows * d.out_row_words);
   I red_total = 1;
   for (int q = 0; q < d.nred; ++q) red_total *= (I)d.red_res[q];
+  auto src_of = [&](I ow) -> I {
+    I rest = ow, src = 0;
+    for (int a = d.nu - 1; a >= 0; --a) {
+      const I r = (I)d.u_res[a];
+      const I q = rest / r;
+      src += (rest - q * r) * (I)d.u_in[a];
+      rest = q;
+    }
+    return src;
+  };
+  if (red_total == 1) {
+    // a pure permutation of words: four loads in flight per thread
+    const I stride = (I)rc.nblk * blockDim.x;
+    I ow = (I)rc.bid * blockDim.x + threadIdx.x;
+    for (; ow + 3 * stride < total; ow += 4 * stride) {
+      uint64_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = d.in[src_of(ow + (I)k * stride)];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d.out[ow + (I)k * stride] = v[k];
+    }
+    for (; ow < total; ow += stride) d.out[ow] = d.in[src_of(ow)];
+    return;
+  }
   for (I ow = (I)rc.bid * blockDim.x + threadIdx.x; ow < total; ow += (I)rc.nblk * blockDim.x) {
     I rest = ow, src = 0;
     for (int a = d.nu - 1; a >= 0; --a) {
@@ -184,28 +208,54 @@ reshape_transpose_kernel(const ReshapeDesc* __restrict__ descs, const int64_t* _
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t nJT = (d.tQ + 255) / 256, nLT = (d.tR + 255) / 256;
   const int64_t tiles = d.n_other * nJT * nLT;
-  for (int64_t tile = rc.bid; tile < tiles; tile += rc.nblk) {
-    const int64_t lt = tile % nLT, r = tile / nLT, jt = r % nJT;
-    int64_t rest = r / nJT, base_in = 0, base_out = 0;
+  // tile -> (L tile, J tile, first input and output word of its other axes)
+  auto locate = [&](int64_t tile, int64_t& lt, int64_t& jt, int64_t& base_in, int64_t& base_out) {
+    lt = tile % nLT;
+    const int64_t r = tile / nLT;
+    jt = r % nJT;
+    int64_t rest = r / nJT;
+    base_in = 0;
+    base_out = 0;
     for (int a = d.nu - 1; a >= 0; --a) {
       const int64_t v = rest % d.u_res[a];
       rest /= d.u_res[a];
       base_in += v * d.u_in[a];
       base_out += v * d.u_out[a];
     }
+  };
+  // the four input words this thread loads for a tile
+  auto load = [&](int64_t lt, int64_t jt, int64_t base_in, uint64_t* v) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int idx = tid + 256 * i, b = idx >> 2, c = idx & 3;
       const int64_t L = lt * 256 + b, jb = jt * 4 + c;
-      uint64_t v = 0;
-      if (L < d.tR && jb * 64 < d.tQ) v = d.in[base_in + L * d.t_in_L + jb];
-      s_in[b * kTrPad + c] = v;
+      v[i] = (L < d.tR && jb * 64 < d.tQ) ? d.in[base_in + L * d.t_in_L + jb] : 0ull;
+    }
+  };
+  // the next tile's loads are issued before the current tile is transposed
+  // and stored, so that their latency overlaps that work
+  int64_t lt = 0, jt = 0, base_in = 0, base_out = 0;
+  uint64_t nv[4] = {0, 0, 0, 0};
+  if (rc.bid < tiles) {
+    locate(rc.bid, lt, jt, base_in, base_out);
+    load(lt, jt, base_in, nv);
+  }
+  for (int64_t tile = rc.bid; tile < tiles; tile += rc.nblk) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + 256 * i, b = idx >> 2, c = idx & 3;
+      s_in[b * kTrPad + c] = nv[i];
+    }
+    const int64_t clt = lt, cjt = jt, cbase_out = base_out;
+    if (tile + rc.nblk < tiles) {
+      locate(tile + rc.nblk, lt, jt, base_in, base_out);
+      load(lt, jt, base_in, nv);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int k = warp * 2 + i, cw = k >> 2, lw = k & 3;
-      if ((jt * 4 + cw) * 64 < d.tQ && lt * 256 + lw * 64 < d.tR) {
+      if ((cjt * 4 + cw) * 64 < d.tQ && clt * 256 + lw * 64 < d.tR) {
         uint64_t lo = s_in[(lw * 64 + lane) * kTrPad + cw];
         uint64_t hi = s_in[(lw * 64 + lane + 32) * kTrPad + cw];
         transpose64(lo, hi, lane);
@@ -217,8 +267,8 @@ reshape_transpose_kernel(const ReshapeDesc* __restrict__ descs, const int64_t* _
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int idx = tid + 256 * i, t = idx >> 2, w = idx & 3;
-      const int64_t J = jt * 256 + t, lw = lt * 4 + w;
-      if (J < d.tQ && lw * 64 < d.tR) d.out[base_out + J * d.t_out_J + lw] = s_out[t * kTrPad + w];
+      const int64_t J = cjt * 256 + t, lw = clt * 4 + w;
+      if (J < d.tQ && lw * 64 < d.tR) d.out[cbase_out + J * d.t_out_J + lw] = s_out[t * kTrPad + w];
     }
     __syncthreads();
   }
