@@ -44,6 +44,11 @@ def test_repeat_and_change_in_place(eng, orc):
     st2 = solve_into(eng, sysm, out)  # same arguments: the kept program runs again
     check_same(out, want, "repeated call")
     assert st1 == st2
+    # from the second equal call on, the kept launches replay as one graph
+    for k in range(3):
+        out.words.zero_()
+        solve_into(eng, sysm, out)
+        check_same(out, want, f"graph replay {k}")
     # new coefficient values in the same arrays: a different program
     for r in sysm.rels:
         r.coeffs[:] = r.coeffs * -1.0 + 0.125
@@ -97,3 +102,24 @@ def test_learned_order_not_kept(eng, orc):
         eng.sync()
         check_same(out, want, "learned order")
     m.close()
+
+
+def test_calls_queued_ahead(eng, orc):
+    """Many calls enqueued without waiting (the host runs ahead of the device
+    through the ring of descriptor staging slots), alternating between two
+    systems and two outputs each: every output ends equal to the oracle's."""
+    a = W.chain(res=256, nrel=4, seed=73)
+    b = W.chain(res=192, nrel=5, seed=74)
+    want_a = orc.solve(a.axes, a.rels, a.exposed).data
+    want_b = orc.solve(b.axes, b.rels, b.exposed).data
+    outs_a = [fresh_out(a) for _ in range(2)]
+    outs_b = [fresh_out(b) for _ in range(2)]
+    for k in range(12):
+        pa.pa_solve_network(eng.ctx, a.axes, a.rels, a.exposed, outs_a[k % 2])
+        pa.pa_solve_network(eng.ctx, a.axes, a.rels, a.exposed, outs_a[k % 2])
+        pa.pa_solve_network(eng.ctx, b.axes, b.rels, b.exposed, outs_b[k % 2])
+    eng.sync()
+    for o in outs_a:
+        check_same(o, want_a, "queued a")
+    for o in outs_b:
+        check_same(o, want_b, "queued b")
