@@ -200,9 +200,10 @@ class _NetArgs:
             return False
         if [tuple(a) for a in axes] != self.axes_val or tuple(exposed) != self.exposed_val:
             return False
-        for r, (vs, deg, kind, eps), c in zip(rels, self.rels_val, self.coeffs):
+        for r, (vs, deg, kind, eps, rule), c in zip(rels, self.rels_val, self.coeffs):
             if (r.coeffs is not c or not c.flags.c_contiguous or c.dtype != np.float64
-                    or tuple(r.vars) != vs or r.degree != deg or r.kind != kind or r.eps != eps):
+                    or tuple(r.vars) != vs or r.degree != deg or r.kind != kind or r.eps != eps
+                    or getattr(r, "rule", 0) != rule):
                 return False
         return True
 
@@ -218,7 +219,7 @@ def _network_args(axes, rels, exposed) -> _NetArgs:
     n = _NetArgs()
     n.axes_ref, n.rels_ref = axes, rels
     n.axes_val = [tuple(a) for a in axes]
-    n.rels_val = [(tuple(r.vars), r.degree, r.kind, r.eps) for r in rels]
+    n.rels_val = [(tuple(r.vars), r.degree, r.kind, r.eps, getattr(r, "rule", 0)) for r in rels]
     n.exposed_val = tuple(exposed)
     n.c_axes = _axes(axes)
     n.c_rels, keep = _relations(rels)

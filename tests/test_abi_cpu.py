@@ -174,6 +174,10 @@ def test_solve_argument_reuse():
     s.rels[1].eps = 0.5
     a2 = pa._network_args(s.axes, s.rels, s.exposed)
     assert a2 is not a1 and a2.c_rels[1].eps == 0.5
+    s.rels[1].rule = W.RULE_CORNER
+    a2b = pa._network_args(s.axes, s.rels, s.exposed)
+    assert a2b is not a2 and a2b.c_rels[1].rule == W.RULE_CORNER
+    a2 = a2b
     s.rels[1].vars = (2, 1)
     a3 = pa._network_args(s.axes, s.rels, s.exposed)
     assert a3 is not a2 and list(a3.c_rels[1].vars)[:2] == [2, 1]
