@@ -235,19 +235,41 @@ def _network_args(axes, rels, exposed) -> _NetArgs:
     return n
 
 
+_OPTS_CACHE = {}
+
+
+def _array_c(a: BitArray) -> PaArray:
+    """a.c(), kept on the object while its words, vars and res stay the same
+    (the library only reads the structure)."""
+    ptr = a.words.data_ptr()
+    cached = a.__dict__.get("_c_cache")
+    if cached is not None and cached[0] == ptr and cached[1] == (a.vars, a.res):
+        return cached[2]
+    c = a.c()
+    a.__dict__["_c_cache"] = (ptr, (a.vars, a.res), c)
+    return c
+
+
 def pa_solve_network(ctx, axes, rels, exposed, out: BitArray, order="greedy", pairs=None,
                      strict=False, stream=None, model=None) -> dict:
     na = _network_args(axes, rels, exposed)
     r = na.c_rels
-    opts = _opts(order, strict, model)
     pr = None
+    if pairs is None and model is None:
+        # options without pairs or a model are constant structures: built once
+        key = (order, bool(strict))
+        opts = _OPTS_CACHE.get(key)
+        if opts is None:
+            opts = _OPTS_CACHE[key] = _opts(order, strict)
+    else:
+        opts = _opts(order, strict, model)
     if pairs is not None:
         flat = [int(v) for p in pairs for v in p]
         pr = _i32(flat)
         opts.npairs = len(pairs)
         opts.pairs = ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32))
     st = PaStats()
-    o = out.c()
+    o = _array_c(out)
     _check(_lib().pa_solve_network(ctx, len(axes), na.c_axes, len(rels), r, len(exposed),
                                    na.c_exposed, ctypes.byref(opts), ctypes.byref(o),
                                    ctypes.byref(st), _stream_ptr(stream)), ctx)
