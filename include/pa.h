@@ -70,7 +70,7 @@ extern "C" {
 typedef enum {
   PA_OK = 0,
   PA_ERR_INVALID_ARG = 1, /* a null pointer, a bad size, inconsistent shapes */
-  PA_ERR_UNSUPPORTED = 2, /* valid input outside this build's limits */
+  PA_ERR_UNSUPPORTED = 2, /* valid input outside the library's limits */
   PA_ERR_TOO_LARGE = 3,   /* an array or index would overflow 2^62 bits */
   PA_ERR_OOM = 4,         /* the workspace could not be allocated */
   PA_ERR_CUDA = 5,        /* a CUDA call failed; see pa_last_error */

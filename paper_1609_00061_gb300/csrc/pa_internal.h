@@ -196,7 +196,7 @@ int64_t reshape_blocks(const ReshapeDesc& d);
 void launch_reshape(const ReshapeDesc* d_descs, const int64_t* d_cta0, int n, int kind,
                     int64_t grid, cudaStream_t s);
 
-// cudaSuccess when this build holds kernel code the current device can run
+// cudaSuccess when the library holds kernel code the current device can run
 cudaError_t probe_kernel_image();
 
 // Clusters that are not matrix products, batched like the contractions:
