@@ -16,7 +16,10 @@
 // (128-byte swizzle) into a 4-deep ring, one elected thread issues
 // tcgen05.mma kind::f8f6f4 (M = 128, N = BN, K = 32 per instruction) into a
 // TMEM accumulator of 128 lanes x BN FP32 columns, and four epilogue warps read
-// it back with tcgen05.ld, compare with zero and store bit-packed rows.  Every
+// it back with tcgen05.ld, compare with zero and store bit-packed rows.  A
+// product with few output tiles and a long K splits K over several CTAs per
+// tile, whose bits are OR-ed into C (cleared beforehand): partial sums combine
+// by OR because each is positive exactly when one of its products is.  Every
 // wait on an mbarrier is bounded (about 1 s); on expiry the kernel sets the
 // error word, finishes without storing and frees its TMEM.  (Expanding inside
 // the contraction kernel instead re-expands every A tile once per column tile
