@@ -360,13 +360,16 @@ pa_status pa_contract_count(pa_ctx* ctx, const pa_array* A, const pa_array* B, i
  * the order chosen by opts->order, and leave the array over `exposed` (in that
  * axis order) in `out`.  nexposed = 0 gives one bit: does the system have a
  * solution pixel.  opts and stats may be NULL.  The order is planned on the
- * host from the shapes alone, so the call never waits for the device.
+ * host from the shapes alone; the call waits for the device only when the
+ * host is more than four calls ahead of it (the descriptor uploads go through
+ * four pinned staging slots).
  * The context keeps the program of its last call: a call whose arguments (the
  * coefficients included, compared by value), stream and output pointer, and
  * the context's path, rates, join logs and profiling state, are all the same
- * skips planning and launches that program again.  Every call still reads the
- * host coefficients, uploads its descriptors and runs every kernel.  Orders of
- * PA_ORDER_LEARNED are never kept (the model may change between calls). */
+ * skips planning and launches that program again (from the second such call
+ * on, as one CUDA graph).  Every call still reads the host coefficients,
+ * uploads its descriptors and runs every kernel.  Orders of PA_ORDER_LEARNED
+ * are never kept (the model may change between calls). */
 pa_status pa_solve_network(pa_ctx* ctx, int32_t nvars, const pa_axis* axes, int32_t nrel,
                            const pa_relation* rels, int32_t nexposed, const int32_t* exposed,
                            const pa_options* opts, pa_array* out, pa_stats* stats,
